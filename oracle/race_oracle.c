@@ -1,0 +1,755 @@
+/*
+ * CPU ORACLE — TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously-correct reference for the SymmSpMV library.  Only
+ * the test-suite, the smoke check and the benchmark's CPU-baseline leg may
+ * load this file's shared object; the library itself never does, and shares
+ * no code with it.
+ *
+ * Paper: Alappat et al., "A Recursive Algebraic Coloring Technique for
+ * Hardware-Efficient Symmetric Sparse Matrix-Vector Multiplication"
+ * (arXiv 1907.06487).  Section/algorithm/equation names below refer to it.
+ *
+ * Numeric part (FP64 throughout):
+ *   orc_expand_full    symmetric expansion of upper CRS into full CRS
+ *   orc_spmv_full      Alg. "SpMV using the CRS format" (b = A x), plus the
+ *                      per-row scale s_i = sum_j |a_ij||x_j| used by the
+ *                      parity bound |b_i - b_ref_i| <= tol * s_i
+ *   orc_symm_spmv      Alg. "SymmSpMV" executed serially (b zeroed first)
+ *   orc_spmv_sampled   b_i and s_i of the plain definition for chosen rows
+ *                      only, in one pass over the upper CRS
+ *
+ * Schedule part (integer + FP64 control arithmetic), Section 4:
+ *   level construction (Alg. "Construction of levels", Eq. "level"),
+ *   level-group pairing by the epsilon rule (Sec. 4.4.3 steps 1-3),
+ *   red/blue split and load balancing with worker weights (Alg. "Load
+ *   Balancing", Sec. 4.3 and 4.4.3 step 4), recursion into level groups with
+ *   the distance-1 halo (Sec. 4.4.2), the RACE tree, effective row counts and
+ *   parallel efficiency eta (Sec. 5), and a flattening of the tree into
+ *   globally synchronised phases.
+ *
+ * Readings taken where the paper is silent or garbled (each one is listed
+ * in the design notes of the repository):
+ *   R1 root of a (sub)graph = its last vertex in the current order
+ *      (Alg. "Construction of levels" sets root = n).
+ *   R2 BFS runs until the frontier is empty; unvisited vertices of the group
+ *      restart from the last unvisited one at (max level so far) + 2
+ *      (islands, Sec. 4.4.1).
+ *   R3 inside a level vertices keep their current relative order.
+ *   R4 weight a = (sum of sizes) * n_t(parent) / size(parent), one FP64
+ *      division of exact integers; b = max(1, round-half-away(a));
+ *      eps = 1 - |a - b|; acceptance eps > eps_s (strict).
+ *   R5 a pair needs >= 2k levels and eps > eps_s; afterwards it grows only
+ *      while a' <= b, keeping the strictly best eps (first wins ties).
+ *      Remaining levels that cannot form a pair, fewer than 2k levels left,
+ *      or threads used up: the rest joins the last pair, which gets all
+ *      remaining threads.
+ *   R6 red gets floor(n/2) levels of a pair, blue the rest.
+ *   R7 load balancing: u_i = size_i / worker_i, mean_c = sum size / sum
+ *      worker over colour c, var = sum diff^2 / len (left to right); the
+ *      group index is absRankIdx[currRank]; shift(src->dst) moves one level
+ *      from src to dst and slides the groups between them.
+ *   R8 recursion into every group with > 1 thread while the stage limit
+ *      allows; sub-graph = group plus its distance-1 halo (k = 2).
+ *   R9 phases: P(leaf)=1, P(node) = max P over red children + max P over
+ *      blue children; red children start at the node's offset, blue ones
+ *      after the red block.  Empty leaves are not listed.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ====================================================================== */
+/* Numeric oracle                                                          */
+/* ====================================================================== */
+
+/* Full symmetric CRS from upper CRS.  frp has n+1 entries; fci/fva must
+ * hold 2*nnz_u - n_diag entries.  Columns of each full row come out sorted
+ * (lower part first in increasing row order, then the upper part).       */
+int64_t orc_expand_full(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                        int64_t *frp, int32_t *fci, double *fva) {
+    int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cnt) return -1;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            cnt[i]++;
+            if (ci[t] != i) cnt[ci[t]]++;
+        }
+    frp[0] = 0;
+    for (int32_t i = 0; i < n; ++i) frp[i + 1] = frp[i] + cnt[i];
+    for (int32_t i = 0; i < n; ++i) cnt[i] = frp[i];
+    /* lower part: entry (i,j) of row i with j>i appears as (j,i) in row j;
+       visiting i in increasing order appends in increasing column order. */
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            int32_t j = ci[t];
+            if (j != i) { fci[cnt[j]] = i; fva[cnt[j]] = va[t]; cnt[j]++; }
+        }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            fci[cnt[i]] = ci[t]; fva[cnt[i]] = va[t]; cnt[i]++;
+        }
+    int64_t nnz = frp[n];
+    free(cnt);
+    return nnz;
+}
+
+/* Alg. "SpMV using the CRS format": b[row] = sum_idx A[idx]*x[col[idx]].
+ * Also s[row] = sum |A[idx]|*|x[col[idx]]| (NULL to skip).                */
+void orc_spmv_full(int32_t n, const int64_t *frp, const int32_t *fci, const double *fva,
+                   const double *x, double *b, double *s) {
+    for (int32_t row = 0; row < n; ++row) {
+        double tmp = 0.0, a = 0.0;
+        for (int64_t idx = frp[row]; idx < frp[row + 1]; ++idx) {
+            tmp += fva[idx] * x[fci[idx]];
+            a += fabs(fva[idx]) * fabs(x[fci[idx]]);
+        }
+        b[row] = tmp;
+        if (s) s[row] = a;
+    }
+}
+
+/* SpMM with a row-major n x k block: B[:,c] = A X[:,c] column by column.  */
+void orc_spmm_full(int32_t n, const int64_t *frp, const int32_t *fci, const double *fva,
+                   int32_t k, const double *X, double *B, double *S) {
+    for (int32_t row = 0; row < n; ++row)
+        for (int32_t c = 0; c < k; ++c) {
+            double tmp = 0.0, a = 0.0;
+            for (int64_t idx = frp[row]; idx < frp[row + 1]; ++idx) {
+                double xv = X[(int64_t)fci[idx] * k + c];
+                tmp += fva[idx] * xv;
+                a += fabs(fva[idx]) * fabs(xv);
+            }
+            B[(int64_t)row * k + c] = tmp;
+            if (S) S[(int64_t)row * k + c] = a;
+        }
+}
+
+/* Alg. "SymmSpMV" run serially; the algorithm accumulates with +=, so b
+ * starts at zero.  The diagonal is the first entry of each row.           */
+void orc_symm_spmv(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                   const double *x, double *b) {
+    for (int32_t i = 0; i < n; ++i) b[i] = 0.0;
+    for (int32_t row = 0; row < n; ++row) {
+        int32_t diag_idx = rp[row];
+        b[row] += va[diag_idx] * x[row];
+        double tmp = 0.0;
+        for (int32_t idx = rp[row] + 1; idx < rp[row + 1]; ++idx) {
+            tmp += va[idx] * x[ci[idx]];
+            b[ci[idx]] += va[idx] * x[row];
+        }
+        b[row] += tmp;
+    }
+}
+
+/* b_i = sum_j a_ij x_j and s_i = sum_j |a_ij||x_j| of the symmetric matrix
+ * for the rows listed in rows[0..m), reading the upper CRS once.  Works on
+ * a k-column row-major block (k=1 for a vector); outputs are m x k.       */
+int orc_spmv_sampled(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                     int32_t k, const double *X, int32_t m, const int32_t *rows,
+                     double *B, double *S) {
+    int32_t *slot = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!slot) return -1;
+    for (int32_t i = 0; i < n; ++i) slot[i] = -1;
+    for (int32_t q = 0; q < m; ++q) {
+        if (rows[q] < 0 || rows[q] >= n || slot[rows[q]] != -1) { free(slot); return -2; }
+        slot[rows[q]] = q;
+    }
+    for (int64_t q = 0; q < (int64_t)m * k; ++q) { B[q] = 0.0; S[q] = 0.0; }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            int32_t j = ci[t];
+            double a = va[t];
+            if (slot[i] >= 0)       /* a_ij x_j contributes to row i */
+                for (int32_t c = 0; c < k; ++c) {
+                    double xv = X[(int64_t)j * k + c];
+                    B[(int64_t)slot[i] * k + c] += a * xv;
+                    S[(int64_t)slot[i] * k + c] += fabs(a) * fabs(xv);
+                }
+            if (j != i && slot[j] >= 0)   /* symmetric partner a_ji = a_ij */
+                for (int32_t c = 0; c < k; ++c) {
+                    double xv = X[(int64_t)i * k + c];
+                    B[(int64_t)slot[j] * k + c] += a * xv;
+                    S[(int64_t)slot[j] * k + c] += fabs(a) * fabs(xv);
+                }
+        }
+    free(slot);
+    return 0;
+}
+
+/* Canonical upper CRS from rows of (col,val) with col >= row in any order:
+ * explicit 0.0 diagonal when missing, diagonal first, increasing columns.
+ * Returns nnz of the output, -1 on an entry below the diagonal or a
+ * duplicate.  Output arrays must hold nnz_in + n entries.                 */
+static int cmp_pair(const void *a, const void *b) {
+    const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+    return (x[0] > y[0]) - (x[0] < y[0]);
+}
+int64_t orc_canonicalize(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                         int32_t *orp, int32_t *oci, double *ova) {
+    int64_t k = 0;
+    int64_t maxrow = 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] - rp[i] > maxrow) maxrow = rp[i + 1] - rp[i];
+    int64_t *buf = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(maxrow + 1));
+    if (!buf) return -2;
+    for (int32_t i = 0; i < n; ++i) {
+        orp[i] = (int32_t)k;
+        int32_t len = rp[i + 1] - rp[i];
+        int has_diag = 0;
+        for (int32_t t = 0; t < len; ++t) {
+            int32_t c = ci[rp[i] + t];
+            if (c < i || c >= n) { free(buf); return -1; }
+            if (c == i) has_diag = 1;
+            buf[2 * t] = c; buf[2 * t + 1] = rp[i] + t;
+        }
+        qsort(buf, (size_t)len, 2 * sizeof(int64_t), cmp_pair);
+        for (int32_t t = 1; t < len; ++t)
+            if (buf[2 * t] == buf[2 * t - 2]) { free(buf); return -1; }
+        if (!has_diag) { oci[k] = i; ova[k] = 0.0; ++k; }
+        for (int32_t t = 0; t < len; ++t) { oci[k] = (int32_t)buf[2 * t]; ova[k] = va[buf[2 * t + 1]]; ++k; }
+    }
+    orp[n] = (int32_t)k;
+    free(buf);
+    return k;
+}
+
+/* ====================================================================== */
+/* Schedule oracle                                                         */
+/* ====================================================================== */
+
+typedef struct {
+    int32_t parent, stage, color, lo, hi, nthreads, thread_lo, nlev, nsub;
+    int32_t first_child, nchildren, phase_count, phase_off;
+    int64_t size, neff;
+} onode;
+
+typedef struct {
+    int32_t n, nt, k, balance, max_depth;
+    double eps[8];
+    /* graph: full adjacency without self loops */
+    int64_t *aptr; int32_t *adj;
+    int64_t *vw;           /* vertex size in the balancing unit */
+    /* current order */
+    int32_t *order, *pos;
+    /* BFS scratch */
+    int32_t *dist, *tmark, *hmark, *dmark, *curr, *next;
+    int32_t stamp;
+    /* tree */
+    onode *nodes; int32_t nnodes, capnodes;
+    /* phases */
+    int32_t nphases, nleaves;
+    int32_t *stage_ptr, *leaf_lo, *leaf_hi, *leaf_node;
+    double eta;
+    int err;
+} osched;
+
+static int32_t new_node(osched *S) {
+    if (S->nnodes == S->capnodes) {
+        S->capnodes = S->capnodes ? 2 * S->capnodes : 64;
+        S->nodes = (onode *)realloc(S->nodes, sizeof(onode) * (size_t)S->capnodes);
+    }
+    memset(&S->nodes[S->nnodes], 0, sizeof(onode));
+    S->nodes[S->nnodes].first_child = -1;
+    return S->nnodes++;
+}
+
+/* Level construction on the group order[lo..hi) (Alg. "Construction of
+ * levels", Eq. "level"), restricted to the group plus its distance-1 halo
+ * unless whole_graph.  Rewrites order[lo..hi) level by level (R3) and
+ * returns the number of levels; *lsize receives per-level sizes in the
+ * balancing unit and *lrows per-level row counts (caller frees).          */
+static int32_t build_levels(osched *S, int32_t lo, int32_t hi, int whole_graph,
+                            int64_t **lsize, int32_t **lrows) {
+    int32_t st = ++S->stamp;
+    for (int32_t p = lo; p < hi; ++p) S->tmark[S->order[p]] = st;
+    if (!whole_graph)
+        for (int32_t p = lo; p < hi; ++p) {
+            int32_t v = S->order[p];
+            S->hmark[v] = st;
+            for (int64_t e = S->aptr[v]; e < S->aptr[v + 1]; ++e) S->hmark[S->adj[e]] = st;
+        }
+    int32_t remaining = hi - lo, scan = hi - 1, maxlvl = -1;
+    while (remaining > 0) {
+        while (S->dmark[S->order[scan]] == st) --scan;       /* R1/R2 */
+        int32_t root = S->order[scan];
+        int32_t lvl = (maxlvl < 0) ? 0 : maxlvl + 2;
+        S->dmark[root] = st; S->dist[root] = lvl;
+        if (S->tmark[root] == st) --remaining;
+        if (lvl > maxlvl) maxlvl = lvl;
+        int32_t nc = 1; S->curr[0] = root;
+        while (nc > 0) {
+            int32_t nn = 0;
+            for (int32_t q = 0; q < nc; ++q) {
+                int32_t u = S->curr[q];
+                for (int64_t e = S->aptr[u]; e < S->aptr[u + 1]; ++e) {
+                    int32_t w = S->adj[e];
+                    if (!whole_graph && S->hmark[w] != st) continue;
+                    if (S->dmark[w] == st) continue;
+                    S->dmark[w] = st; S->dist[w] = lvl + 1;
+                    if (S->tmark[w] == st) --remaining;
+                    S->next[nn++] = w;
+                }
+            }
+            if (nn > 0 && lvl + 1 > maxlvl) maxlvl = lvl + 1;
+            int32_t *t = S->curr; S->curr = S->next; S->next = t;
+            nc = nn; ++lvl;
+        }
+    }
+    int32_t nlev = 0;
+    for (int32_t p = lo; p < hi; ++p)
+        if (S->dist[S->order[p]] + 1 > nlev) nlev = S->dist[S->order[p]] + 1;
+    int64_t *sz = (int64_t *)calloc((size_t)nlev + 1, sizeof(int64_t));
+    int32_t *rows = (int32_t *)calloc((size_t)nlev + 1, sizeof(int32_t));
+    int32_t *start = (int32_t *)calloc((size_t)nlev + 1, sizeof(int32_t));
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(hi - lo + 1));
+    for (int32_t p = lo; p < hi; ++p) {
+        int32_t v = S->order[p], d = S->dist[v];
+        rows[d]++; sz[d] += S->vw[v];
+    }
+    for (int32_t l = 1; l <= nlev; ++l) start[l] = start[l - 1] + rows[l - 1];
+    for (int32_t p = lo; p < hi; ++p) {                       /* stable: R3 */
+        int32_t v = S->order[p];
+        tmp[start[S->dist[v]]++] = v;
+    }
+    for (int32_t p = lo; p < hi; ++p) { S->order[p] = tmp[p - lo]; S->pos[S->order[p]] = p; }
+    free(tmp); free(start);
+    *lsize = sz; *lrows = rows;
+    return nlev;
+}
+
+/* Sec. 4.4.3 steps 1-3 (R4, R5): pairs of level groups with thread counts.
+ * Writes pair boundaries pb[0..np] (level indices) and threads pt[0..np).  */
+static int32_t make_pairs(const int64_t *sz, int32_t nlev, int32_t nt, double eps, int32_t k,
+                          int32_t *pb, int32_t *pt) {
+    int64_t tot = 0;
+    for (int32_t l = 0; l < nlev; ++l) tot += sz[l];
+    int32_t np = 0, start = 0, assigned = 0;
+    pb[0] = 0;
+    while (start < nlev) {
+        int64_t s = 0;
+        int32_t end = start, found = 0;
+        double a = 0.0, b = 0.0, e = 0.0;
+        while (end < nlev) {
+            s += sz[end]; ++end;
+            a = tot > 0 ? (double)(s * (int64_t)nt) / (double)tot : 0.0;
+            b = round(a); if (b < 1.0) b = 1.0;
+            e = 1.0 - fabs(a - b);
+            if (end - start >= 2 * k && e > eps) { found = 1; break; }
+        }
+        if (!found) {                      /* rest joins the last pair (R5) */
+            if (np > 0) { assigned -= pt[np - 1]; pt[np - 1] = nt - assigned; pb[np] = nlev; }
+            else { pt[0] = nt; pb[1] = nlev; np = 1; }
+            return np;
+        }
+        int32_t best_end = end; double best_e = e;
+        while (end < nlev) {
+            s += sz[end]; ++end;
+            double a2 = (double)(s * (int64_t)nt) / (double)tot;
+            if (a2 > b) break;
+            double e2 = 1.0 - fabs(a2 - b);
+            if (e2 > best_e) { best_e = e2; best_end = end; }
+        }
+        int32_t bi = (int32_t)b;
+        if (nlev - best_end < 2 * k || assigned + bi >= nt) {
+            pt[np] = nt - assigned; pb[np + 1] = nlev; ++np;
+            return np;
+        }
+        pt[np] = bi; pb[np + 1] = best_end; ++np;
+        assigned += bi; start = best_end;
+    }
+    return np;
+}
+
+typedef struct { double key; int32_t idx; } kv;
+static int cmp_kv(const void *a, const void *b) {
+    const kv *x = (const kv *)a, *y = (const kv *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+static double lb_variance(const int64_t *pre, const int32_t *tp, const int32_t *worker, int32_t len,
+                          double *diff) {
+    int64_t tot[2] = {0, 0}, wk[2] = {0, 0};
+    for (int32_t i = 0; i < len; ++i) { tot[i & 1] += pre[tp[i + 1]] - pre[tp[i]]; wk[i & 1] += worker[i]; }
+    double mean[2];
+    for (int c = 0; c < 2; ++c) mean[c] = wk[c] > 0 ? (double)tot[c] / (double)wk[c] : 0.0;
+    double var = 0.0;
+    for (int32_t i = 0; i < len; ++i) {
+        double u = (double)(pre[tp[i + 1]] - pre[tp[i]]) / (double)worker[i];
+        diff[i] = u - mean[i & 1];
+        var += diff[i] * diff[i];
+    }
+    return var / (double)len;
+}
+
+static void lb_shift(int32_t *tp, int32_t src, int32_t dst) {
+    if (src > dst) for (int32_t j = dst + 1; j <= src; ++j) tp[j] += 1;
+    else for (int32_t j = src + 1; j <= dst; ++j) tp[j] -= 1;
+}
+
+/* Alg. "Load Balancing" with worker weights (R7). tp has len+1 entries.   */
+static void load_balance(const int64_t *sz, int32_t nlev, int32_t *tp, const int32_t *worker,
+                         int32_t len, int32_t k) {
+    int64_t *pre = (int64_t *)malloc(sizeof(int64_t) * ((size_t)nlev + 1));
+    pre[0] = 0;
+    for (int32_t l = 0; l < nlev; ++l) pre[l + 1] = pre[l] + sz[l];
+    double *diff = (double *)malloc(sizeof(double) * (size_t)len);
+    double *diff2 = (double *)malloc(sizeof(double) * (size_t)len);
+    int32_t *absRank = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+    int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+    int32_t *old = (int32_t *)malloc(sizeof(int32_t) * ((size_t)len + 1));
+    kv *srt = (kv *)malloc(sizeof(kv) * (size_t)len);
+    for (;;) {
+        double var = lb_variance(pre, tp, worker, len, diff);
+        for (int32_t i = 0; i < len; ++i) { srt[i].key = -fabs(diff[i]); srt[i].idx = i; }
+        qsort(srt, (size_t)len, sizeof(kv), cmp_kv);
+        for (int32_t i = 0; i < len; ++i) absRank[i] = srt[i].idx;
+        for (int32_t i = 0; i < len; ++i) { srt[i].key = diff[i]; srt[i].idx = i; }
+        qsort(srt, (size_t)len, sizeof(kv), cmp_kv);
+        for (int32_t i = 0; i < len; ++i) rank[i] = srt[i].idx;
+        memcpy(old, tp, sizeof(int32_t) * ((size_t)len + 1));
+        int32_t currRank = 0;
+        double newVar = var;
+        int improved = 0;
+        while (newVar >= var) {
+            memcpy(tp, old, sizeof(int32_t) * ((size_t)len + 1));
+            int fail = 1;
+            int32_t t = absRank[currRank];
+            if (diff[t] < 0.0) {
+                for (int32_t q = len - 1; q >= 0; --q) {
+                    int32_t el = rank[q];
+                    if (el != t && tp[el + 1] - tp[el] > k) { lb_shift(tp, el, t); fail = 0; break; }
+                }
+            } else if (tp[t + 1] - tp[t] > k) {
+                int32_t g = rank[0];
+                if (g != t) { lb_shift(tp, t, g); fail = 0; }
+            }
+            if (!fail) newVar = lb_variance(pre, tp, worker, len, diff2);
+            if (currRank == len - 1 && newVar >= var) {
+                memcpy(tp, old, sizeof(int32_t) * ((size_t)len + 1));
+                break;
+            }
+            if (newVar < var) { improved = 1; break; }
+            ++currRank;
+        }
+        if (!improved) break;
+    }
+    free(pre); free(diff); free(diff2); free(absRank); free(rank); free(old); free(srt);
+}
+
+/* Split node id (Sec. 4.4.3) and recurse into children with > 1 thread.   */
+static void split_node(osched *S, int32_t id) {
+    onode nd = S->nodes[id];
+    int whole = (nd.parent < 0);
+    int64_t *sz; int32_t *rows;
+    int32_t nlev = build_levels(S, nd.lo, nd.hi, whole, &sz, &rows);
+    S->nodes[id].nsub = nlev;
+    if (nlev < 2 * S->k) { free(sz); free(rows); return; }
+    int32_t s = nd.stage + 1;
+    double eps = S->eps[s < 8 ? s : 7];
+    int32_t *pb = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nlev + 2));
+    int32_t *pt = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nlev + 2));
+    int32_t np = make_pairs(sz, nlev, nd.nthreads, eps, S->k, pb, pt);
+    int32_t len = 2 * np;
+    int32_t *tp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)len + 1));
+    int32_t *worker = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+    for (int32_t p = 0; p < np; ++p) {
+        int32_t n_l = pb[p + 1] - pb[p];
+        tp[2 * p] = pb[p]; tp[2 * p + 1] = pb[p] + n_l / 2;           /* R6 */
+        worker[2 * p] = worker[2 * p + 1] = pt[p];
+    }
+    tp[len] = nlev;
+    load_balance(sz, nlev, tp, worker, len, S->k);
+    /* children, in level order */
+    int32_t first = S->nnodes;
+    int32_t row0 = nd.lo, thr = nd.thread_lo;
+    for (int32_t g = 0; g < len; ++g) {
+        int32_t c = new_node(S);
+        onode *cn = &S->nodes[c];
+        int32_t r = 0; int64_t w = 0;
+        for (int32_t l = tp[g]; l < tp[g + 1]; ++l) { r += rows[l]; w += sz[l]; }
+        cn->parent = id; cn->stage = s; cn->color = g & 1;
+        cn->lo = row0; cn->hi = row0 + r; row0 += r;
+        cn->nthreads = worker[g]; cn->thread_lo = thr;
+        if (g & 1) thr += worker[g];
+        cn->nlev = tp[g + 1] - tp[g]; cn->size = w;
+    }
+    S->nodes[id].first_child = first;
+    S->nodes[id].nchildren = len;
+    free(sz); free(rows); free(pb); free(pt); free(tp); free(worker);
+    for (int32_t g = 0; g < len; ++g) {                                     /* R8 */
+        onode cn = S->nodes[first + g];
+        int allowed = (S->max_depth < 0) || (cn.stage + 1 < S->max_depth);
+        if (cn.nthreads > 1 && allowed && cn.hi > cn.lo) split_node(S, first + g);
+    }
+}
+
+/* Sec. 5: effective row count and phase counts (R9), bottom-up.           */
+static void tree_metrics(osched *S, int32_t id) {
+    onode *nd = &S->nodes[id];
+    if (nd->nchildren == 0) { nd->neff = nd->size; nd->phase_count = 1; return; }
+    int64_t mr = 0, mb = 0; int32_t pr = 0, pbk = 0;
+    for (int32_t g = 0; g < nd->nchildren; ++g) {
+        int32_t c = nd->first_child + g;
+        tree_metrics(S, c);
+        onode *cn = &S->nodes[c];
+        if (cn->color == 0) { if (cn->neff > mr) mr = cn->neff; if (cn->phase_count > pr) pr = cn->phase_count; }
+        else { if (cn->neff > mb) mb = cn->neff; if (cn->phase_count > pbk) pbk = cn->phase_count; }
+    }
+    nd = &S->nodes[id];
+    nd->neff = mr + mb;
+    nd->phase_count = pr + pbk;
+}
+
+static void assign_offsets(osched *S, int32_t id, int32_t off) {
+    onode *nd = &S->nodes[id];
+    nd->phase_off = off;
+    if (nd->nchildren == 0) return;
+    int32_t pr = 0;
+    for (int32_t g = 0; g < nd->nchildren; ++g) {
+        onode *cn = &S->nodes[nd->first_child + g];
+        if (cn->color == 0 && cn->phase_count > pr) pr = cn->phase_count;
+    }
+    int32_t fc = nd->first_child, nc = nd->nchildren;
+    for (int32_t g = 0; g < nc; ++g) {
+        int32_t c = fc + g;
+        assign_offsets(S, c, S->nodes[c].color == 0 ? off : off + pr);
+    }
+}
+
+typedef struct { int32_t phase, lo, node; } leafkey;
+static int cmp_leaf(const void *a, const void *b) {
+    const leafkey *x = (const leafkey *)a, *y = (const leafkey *)b;
+    if (x->phase != y->phase) return (x->phase > y->phase) - (x->phase < y->phase);
+    return (x->lo > y->lo) - (x->lo < y->lo);
+}
+
+void orc_race_free(osched *S);
+
+osched *orc_race(int32_t n, const int32_t *rp, const int32_t *ci, int32_t nt, const double *eps8,
+                 int32_t max_depth, int32_t balance) {
+    if (n <= 0 || nt <= 0) return NULL;
+    osched *S = (osched *)calloc(1, sizeof(osched));
+    S->n = n; S->nt = nt; S->k = 2; S->balance = balance; S->max_depth = max_depth;
+    for (int i = 0; i < 8; ++i) S->eps[i] = eps8[i];
+    /* symmetric adjacency (self loops dropped, Sec. 4 graph definitions) */
+    S->aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { S->aptr[i + 1]++; S->aptr[ci[t] + 1]++; }
+    for (int32_t i = 0; i < n; ++i) S->aptr[i + 1] += S->aptr[i];
+    S->adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S->aptr[n] > 0 ? S->aptr[n] : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    memcpy(fill, S->aptr, sizeof(int64_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { S->adj[fill[i]++] = ci[t]; S->adj[fill[ci[t]]++] = i; }
+    free(fill);
+    S->vw = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        S->vw[i] = balance ? 1 + (S->aptr[i + 1] - S->aptr[i]) : 1;
+    S->order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    S->pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) { S->order[i] = i; S->pos[i] = i; }
+    S->dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    S->tmark = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    S->hmark = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    S->dmark = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    S->curr = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    S->next = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    /* root node T_{-1}(0): all vertices, all threads */
+    int32_t r = new_node(S);
+    S->nodes[r].parent = -1; S->nodes[r].stage = -1; S->nodes[r].color = 0;
+    S->nodes[r].lo = 0; S->nodes[r].hi = n; S->nodes[r].nthreads = nt;
+    int64_t tot = 0;
+    for (int32_t i = 0; i < n; ++i) tot += S->vw[i];
+    S->nodes[r].size = tot;
+    if (max_depth != 0) split_node(S, r);
+    tree_metrics(S, r);
+    assign_offsets(S, r, 0);
+    S->eta = (double)tot / ((double)S->nodes[r].neff * (double)nt);
+    /* flatten: non-empty leaves sorted by (phase, first row) */
+    int32_t nl = 0;
+    for (int32_t i = 0; i < S->nnodes; ++i)
+        if (S->nodes[i].nchildren == 0 && S->nodes[i].hi > S->nodes[i].lo) ++nl;
+    leafkey *lk = (leafkey *)malloc(sizeof(leafkey) * (size_t)(nl > 0 ? nl : 1));
+    nl = 0;
+    for (int32_t i = 0; i < S->nnodes; ++i)
+        if (S->nodes[i].nchildren == 0 && S->nodes[i].hi > S->nodes[i].lo) {
+            lk[nl].phase = S->nodes[i].phase_off; lk[nl].lo = S->nodes[i].lo; lk[nl].node = i; ++nl;
+        }
+    qsort(lk, (size_t)nl, sizeof(leafkey), cmp_leaf);
+    S->nphases = S->nodes[r].phase_count;
+    S->nleaves = nl;
+    S->stage_ptr = (int32_t *)calloc((size_t)S->nphases + 1, sizeof(int32_t));
+    S->leaf_lo = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    S->leaf_hi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    S->leaf_node = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    for (int32_t q = 0; q < nl; ++q) {
+        S->leaf_lo[q] = lk[q].lo; S->leaf_hi[q] = S->nodes[lk[q].node].hi; S->leaf_node[q] = lk[q].node;
+        S->stage_ptr[lk[q].phase + 1]++;
+    }
+    for (int32_t p = 0; p < S->nphases; ++p) S->stage_ptr[p + 1] += S->stage_ptr[p];
+    free(lk);
+    /* scratch no longer needed */
+    free(S->dist); free(S->tmark); free(S->hmark); free(S->dmark); free(S->curr); free(S->next);
+    S->dist = S->tmark = S->hmark = S->dmark = S->curr = S->next = NULL;
+    return S;
+}
+
+void orc_race_free(osched *S) {
+    if (!S) return;
+    free(S->aptr); free(S->adj); free(S->vw); free(S->order); free(S->pos);
+    free(S->dist); free(S->tmark); free(S->hmark); free(S->dmark); free(S->curr); free(S->next);
+    free(S->nodes); free(S->stage_ptr); free(S->leaf_lo); free(S->leaf_hi); free(S->leaf_node);
+    free(S);
+}
+
+/* ---- accessors ---------------------------------------------------------- */
+void orc_race_info(const osched *S, int32_t *info /* 6 */, double *eta) {
+    info[0] = S->n; info[1] = S->nt; info[2] = S->nnodes; info[3] = S->nphases; info[4] = S->nleaves;
+    int32_t depth = 0;
+    for (int32_t i = 0; i < S->nnodes; ++i) if (S->nodes[i].stage + 1 > depth) depth = S->nodes[i].stage + 1;
+    info[5] = depth;
+    *eta = S->eta;
+}
+void orc_race_perm(const osched *S, int32_t *perm) { memcpy(perm, S->order, sizeof(int32_t) * (size_t)S->n); }
+void orc_race_phases(const osched *S, int32_t *stage_ptr, int32_t *lo, int32_t *hi, int32_t *node) {
+    memcpy(stage_ptr, S->stage_ptr, sizeof(int32_t) * ((size_t)S->nphases + 1));
+    memcpy(lo, S->leaf_lo, sizeof(int32_t) * (size_t)S->nleaves);
+    memcpy(hi, S->leaf_hi, sizeof(int32_t) * (size_t)S->nleaves);
+    memcpy(node, S->leaf_node, sizeof(int32_t) * (size_t)S->nleaves);
+}
+/* node table, in creation order: 13 int32 + 2 int64 per node, unpacked   */
+void orc_race_nodes(const osched *S, int32_t *i32 /* 13*nnodes */, int64_t *i64 /* 2*nnodes */) {
+    for (int32_t i = 0; i < S->nnodes; ++i) {
+        const onode *d = &S->nodes[i];
+        int32_t *o = i32 + 13 * (size_t)i;
+        o[0] = d->parent; o[1] = d->stage; o[2] = d->color; o[3] = d->lo; o[4] = d->hi;
+        o[5] = d->nthreads; o[6] = d->thread_lo; o[7] = d->nlev; o[8] = d->nsub;
+        o[9] = d->first_child; o[10] = d->nchildren; o[11] = d->phase_count; o[12] = d->phase_off;
+        i64[2 * (size_t)i] = d->size; i64[2 * (size_t)i + 1] = d->neff;
+    }
+}
+
+/* ---- canonical export (byte layout documented with race_export) -------- */
+static void put32(uint8_t **p, int32_t v) { memcpy(*p, &v, 4); *p += 4; }
+static void put64(uint8_t **p, int64_t v) { memcpy(*p, &v, 8); *p += 8; }
+static void putd(uint8_t **p, double v) { memcpy(*p, &v, 8); *p += 8; }
+
+static void export_node(const osched *S, int32_t id, uint8_t **p) {
+    const onode *d = &S->nodes[id];
+    put32(p, d->stage); put32(p, d->color); put32(p, d->lo); put32(p, d->hi);
+    put32(p, d->nthreads); put32(p, d->thread_lo); put32(p, d->nlev); put32(p, d->nsub);
+    put32(p, d->nchildren); put32(p, d->phase_count); put32(p, d->phase_off);
+    put64(p, d->size); put64(p, d->neff);
+    for (int32_t g = 0; g < d->nchildren; ++g) export_node(S, d->first_child + g, p);
+}
+
+int64_t orc_race_export(const osched *S, uint8_t *buf) {
+    int64_t sz = 4 * 12 + 8 * 9 + 4 * (int64_t)S->n + 4 * ((int64_t)S->nphases + 1) +
+                 8 * (int64_t)S->nleaves + (int64_t)S->nnodes * (11 * 4 + 2 * 8);
+    if (!buf) return sz;
+    uint8_t *p = buf;
+    put32(&p, 0x45434152); put32(&p, 1);
+    put32(&p, S->n); put32(&p, S->nt); put32(&p, S->k); put32(&p, S->balance);
+    put32(&p, S->max_depth); put32(&p, S->nnodes); put32(&p, S->nphases); put32(&p, S->nleaves);
+    put32(&p, 0); put32(&p, 0);
+    for (int i = 0; i < 8; ++i) putd(&p, S->eps[i]);
+    putd(&p, S->eta);
+    for (int32_t i = 0; i < S->n; ++i) put32(&p, S->order[i]);
+    for (int32_t i = 0; i <= S->nphases; ++i) put32(&p, S->stage_ptr[i]);
+    for (int32_t i = 0; i < S->nleaves; ++i) { put32(&p, S->leaf_lo[i]); put32(&p, S->leaf_hi[i]); }
+    export_node(S, 0, &p);
+    return (int64_t)(p - buf);
+}
+
+/* Permuted upper CRS (Sec. 4.1: rows and columns permuted symmetrically):
+ * entry (i,j,a) of the input lands in row min(P(i),P(j)), column max(...),
+ * columns increasing (the diagonal therefore first).  Output arrays hold
+ * nnz_u entries.                                                          */
+int orc_permute_upper(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                      const int32_t *perm, int32_t *orp, int32_t *oci, double *ova) {
+    int32_t *newpos = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!newpos || !cnt) { free(newpos); free(cnt); return -1; }
+    for (int32_t p = 0; p < n; ++p) newpos[perm[p]] = p;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            int32_t a = newpos[i], b = newpos[ci[t]];
+            cnt[(a < b ? a : b) + 1]++;
+        }
+    for (int32_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    for (int32_t i = 0; i <= n; ++i) orp[i] = (int32_t)cnt[i];
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            int32_t a = newpos[i], b = newpos[ci[t]];
+            int32_t r = a < b ? a : b, c = a < b ? b : a;
+            oci[cnt[r]] = c; ova[cnt[r]] = va[t]; cnt[r]++;
+        }
+    /* insertion sort per row (rows are short) */
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = orp[r] + 1; t < orp[r + 1]; ++t) {
+            int32_t c = oci[t]; double v = ova[t]; int32_t u = t - 1;
+            while (u >= orp[r] && oci[u] > c) { oci[u + 1] = oci[u]; ova[u + 1] = ova[u]; --u; }
+            oci[u + 1] = c; ova[u + 1] = v;
+        }
+    free(newpos); free(cnt);
+    return 0;
+}
+
+/* Conflict check of a flattened schedule on the permuted upper CRS: every
+ * row in exactly one leaf, and within a phase the write sets
+ * {rows of the leaf} U {upper columns of those rows} pairwise disjoint.
+ * Returns 0 if valid, 1 = row coverage broken, 2 = write conflict.        */
+int orc_check_phases(int32_t n, const int32_t *prp, const int32_t *pci, int32_t nphases,
+                     const int32_t *stage_ptr, const int32_t *lo, const int32_t *hi) {
+    int32_t *cover = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ophase = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int rc = 0;
+    for (int32_t i = 0; i < n; ++i) { owner[i] = -1; ophase[i] = -1; }
+    for (int32_t ph = 0; ph < nphases && !rc; ++ph)
+        for (int32_t q = stage_ptr[ph]; q < stage_ptr[ph + 1] && !rc; ++q)
+            for (int32_t r = lo[q]; r < hi[q] && !rc; ++r) {
+                if (r < 0 || r >= n) { rc = 1; break; }
+                cover[r]++;
+                for (int32_t t = prp[r]; t < prp[r + 1]; ++t) {
+                    int32_t c = pci[t];
+                    if (ophase[c] == ph && owner[c] != q) { rc = 2; break; }
+                    ophase[c] = ph; owner[c] = q;
+                }
+            }
+    for (int32_t i = 0; i < n && !rc; ++i) if (cover[i] != 1) rc = 1;
+    free(cover); free(owner); free(ophase);
+    return rc;
+}
+
+/* Plain BFS distances on the whole graph from one root (Eq. "level").    */
+int orc_bfs_dist(int32_t n, const int32_t *rp, const int32_t *ci, int32_t root, int32_t *dist) {
+    int64_t *aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { aptr[i + 1]++; aptr[ci[t] + 1]++; }
+    for (int32_t i = 0; i < n; ++i) aptr[i + 1] += aptr[i];
+    int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(aptr[n] + 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    memcpy(fill, aptr, sizeof(int64_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { adj[fill[i]++] = ci[t]; adj[fill[ci[t]]++] = i; }
+    int32_t *q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) dist[i] = -1;
+    int64_t h = 0, t = 0;
+    dist[root] = 0; q[t++] = root;
+    while (h < t) {
+        int32_t u = q[h++];
+        for (int64_t e = aptr[u]; e < aptr[u + 1]; ++e)
+            if (dist[adj[e]] < 0) { dist[adj[e]] = dist[u] + 1; q[t++] = adj[e]; }
+    }
+    free(aptr); free(adj); free(fill); free(q);
+    return 0;
+}
