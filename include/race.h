@@ -1,0 +1,194 @@
+/*
+ * race.h — C ABI of the GB300 SymmSpMV library (RACE-scheduled symmetric
+ * sparse matrix-vector multiplication from upper-triangle CRS storage).
+ *
+ * Paper: C. Alappat et al., "A Recursive Algebraic Coloring Technique for
+ * Hardware-Efficient Symmetric Sparse Matrix-Vector Multiplication",
+ * arXiv 1907.06487.  Section, algorithm and equation names below refer to it.
+ *
+ * General conventions
+ *   - Every entry point returns an int status (RACE_OK = 0 or a RACE_ERR_*
+ *     code); none throws, none traps on the device.  race_strerror() maps a
+ *     code to text.  race_last_error_detail() gives a one-line reason for
+ *     the most recent failure on the calling thread.
+ *   - "host" pointers are CPU memory; "device" pointers are CUDA global
+ *     memory of the current device.  Streams are cudaStream_t passed as
+ *     void* (NULL = legacy default stream).  All device work is enqueued on
+ *     the caller's stream; nothing synchronises the device unless stated.
+ *   - Vectors seen by symm_spmv / symm_spmm / spmv_full are in the
+ *     schedule's PERMUTED order (the paper runs all kernels on the permuted
+ *     matrix, Sec. 4.1 and 6.1).  race_permute / race_unpermute convert.
+ *   - Outputs are overwritten (b = A x), not accumulated.
+ *   - x and b (X and B) must not alias.
+ */
+#ifndef RACE_GB300_H
+#define RACE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define RACE_OK               0
+#define RACE_ERR_INVALID      1  /* malformed input: n <= 0, entry below the
+                                    diagonal, duplicate or out-of-range column,
+                                    non-monotone row_ptr, non-finite value,
+                                    bad parameter, NULL pointer             */
+#define RACE_ERR_OVERFLOW     2  /* a count does not fit the int32 layout   */
+#define RACE_ERR_NOMEM        3  /* host or device allocation failed        */
+#define RACE_ERR_CUDA         4  /* a CUDA runtime call failed              */
+#define RACE_ERR_TIMEOUT      5  /* a bounded device wait gave up           */
+#define RACE_ERR_UNSUPPORTED  6  /* valid request this build does not serve */
+
+/* ---- value types --------------------------------------------------------- */
+#define RACE_F64 0   /* matrix values stored as double                       */
+#define RACE_F32 1   /* matrix values stored as float; products and sums in
+                        double (x, b and accumulation stay FP64)             */
+
+/* ---- balancing unit (Sec. 4.3: rows or nonzeros) ------------------------- */
+#define RACE_BAL_ROWS 0   /* paper default                                   */
+#define RACE_BAL_NNZ  1   /* vertex weight = nonzeros of its full row        */
+
+/* ---- flags for race_params.flags ----------------------------------------- */
+#define RACE_FLAG_HOST_ONLY 1u  /* build the schedule on the host only: no
+                                   device upload (race_export / race_get_info
+                                   work, compute entry points return
+                                   RACE_ERR_UNSUPPORTED).  Needs no GPU.     */
+
+/* Upper-triangle CRS matrix in HOST memory (Sec. 3.2, Alg. "SymmSpMV"):
+ * row i holds the entries (i, j) with j >= i.  Columns may come in any
+ * order within a row; a missing diagonal is treated as an explicit 0.0.
+ * The library copies what it needs; the caller keeps ownership.           */
+typedef struct {
+    int32_t n;              /* number of rows = columns, > 0                 */
+    int64_t nnz;            /* stored entries, = row_ptr[n]                  */
+    const int32_t *row_ptr; /* n+1 offsets, row_ptr[0] = 0, non-decreasing   */
+    const int32_t *col;     /* nnz column indices, row <= col < n            */
+    const void *val;        /* nnz values: double (RACE_F64) or float (F32)  */
+    int32_t val_type;       /* RACE_F64 | RACE_F32                           */
+} race_csr_upper;
+
+/* Parameters of the schedule (Sec. 4.4.3 and 5.1).                          */
+typedef struct {
+    int32_t dist_k;      /* distance of the colouring; must be 2 (SymmSpMV) */
+    int32_t n_workers;   /* N_t: number of schedule workers, >= 1           */
+    double eps[8];       /* epsilon_s for stage s = 0..7 (later stages use
+                            eps[7]); each in [0.5, 1).  Paper's choice:
+                            0.8, 0.8, then 0.5                              */
+    int32_t max_depth;   /* number of stages allowed: 0 = no colouring (one
+                            serial leaf), 1 = stage 0 only, ...; -1 = as
+                            deep as the epsilon rule goes (paper)           */
+    int32_t balance;     /* RACE_BAL_ROWS | RACE_BAL_NNZ                    */
+    int32_t group_lanes; /* lanes that execute one leaf row together on the
+                            GPU: 0 = automatic, else 4, 8, 16 or 32         */
+    uint32_t flags;      /* RACE_FLAG_*                                     */
+} race_params;
+
+/* Summary of a built schedule.                                             */
+typedef struct {
+    int32_t n;           /* rows                                           */
+    int64_t nnz_upper;   /* stored upper entries incl. diagonal            */
+    int32_t n_levels;    /* BFS levels of the whole graph (N_l)            */
+    int32_t n_phases;    /* globally synchronised phases after flattening  */
+    int32_t n_leaves;    /* non-empty leaves over all phases               */
+    int32_t n_nodes;     /* nodes of the RACE tree incl. the root          */
+    int32_t depth;       /* deepest stage + 1                              */
+    int32_t n_workers;   /* N_t                                            */
+    int32_t val_type;    /* RACE_F64 | RACE_F32                            */
+    int32_t group_lanes; /* lanes per leaf row on the GPU                  */
+    double eta;          /* parallel efficiency (Sec. 5: N_r / (N_eff * N_t)) */
+    int64_t neff_root;   /* effective row count of the root (Sec. 5)       */
+} race_info;
+
+typedef struct race_schedule race_schedule;  /* opaque */
+
+/* Set params to the paper's defaults: dist_k 2, eps = {0.8, 0.8, 0.5...},
+ * max_depth -1, balance rows, group_lanes automatic, n_workers given.      */
+void race_default_params(race_params *p, int32_t n_workers);
+
+/* race_build — the RACE preprocessing (Sec. 4): level construction (Alg.
+ * "Construction of levels"), distance-2 level groups with epsilon-driven
+ * thread assignment (Sec. 4.4.3), load balancing (Alg. "Load Balancing"),
+ * recursion with the distance-1 halo (Sec. 4.4.2), the tree and its
+ * efficiency eta (Sec. 5), flattened into phases.  The matrix is permuted
+ * symmetrically and uploaded to the device on `stream` (unless
+ * RACE_FLAG_HOST_ONLY); the call returns after the upload has completed.
+ * On success *out owns host and device copies until race_free.
+ * Errors: RACE_ERR_INVALID, _OVERFLOW, _NOMEM, _CUDA.                      */
+int race_build(const race_csr_upper *a, const race_params *p, void *stream, race_schedule **out);
+
+/* symm_spmv — b = A x for the symmetric A whose upper triangle was given,
+ * i.e. b = A_u x + A_u^T x - diag(A) x (Alg. "SymmSpMV"), run phase by
+ * phase on the device so that no two concurrent workers write the same
+ * entry of b.  x, b: device arrays of n doubles in permuted order.        */
+int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stream);
+
+/* Executors of SymmSpMV (symm_spmv_exec).                                  */
+#define RACE_EXEC_LEAF_GROUP 0  /* one leaf per group of lanes, rows in order,
+                                   plain loads/stores of b (the paper's model:
+                                   a leaf runs on one thread)               */
+#define RACE_EXEC_LEAF_CTA   1  /* one leaf per thread block, the leaf's rows
+                                   in parallel; updates within a leaf are
+                                   reductions at L2; leaves of a phase never
+                                   share an entry of b                      */
+#define RACE_EXEC_ATOMIC     2  /* comparison point: no phases, every update
+                                   a reduction at L2 (ignores the schedule)  */
+
+/* symm_spmv_exec — symm_spmv with an explicit executor (RACE_EXEC_*).
+ * Same arguments, layout and errors as symm_spmv.                          */
+int symm_spmv_exec(const race_schedule *s, int32_t executor, const double *x_d, double *b_d, void *stream);
+
+/* symm_spmm — B = A X for k right-hand sides, X and B row-major n x k
+ * device arrays (element (i, c) at i*k + c) in permuted row order.
+ * 1 <= k <= 16.                                                            */
+int symm_spmm(const race_schedule *s, int32_t k, const double *X_d, double *B_d, void *stream);
+
+/* spmv_full — the traffic baseline: Alg. "SpMV using the CRS format" on the
+ * full (both triangles) CRS of the same permuted matrix, row-parallel, no
+ * schedule.  The full matrix is built and uploaded on the first call (or
+ * by race_prepare_full) and kept with the schedule.  k = 1.               */
+int spmv_full(const race_schedule *s, const double *x_d, double *b_d, void *stream);
+
+/* Build and upload the full CRS used by spmv_full now (optional).          */
+int race_prepare_full(race_schedule *s, void *stream);
+
+/* race_permute: out[new] = in[perm[new]] (original -> permuted order);
+ * race_unpermute: out[perm[new]] = in[new].  in/out: device arrays of n*k
+ * doubles, row-major with k columns; must not alias.                       */
+int race_permute(const race_schedule *s, const double *in_d, double *out_d, int32_t k, void *stream);
+int race_unpermute(const race_schedule *s, const double *in_d, double *out_d, int32_t k, void *stream);
+
+/* Copy the permutation perm[new] = old (n int32) to host memory.          */
+int race_get_perm(const race_schedule *s, int32_t *perm_host);
+
+/* Copy the permuted upper CRS to host memory: row_ptr (n+1), col (nnz),
+ * val (nnz of the stored type).  Any pointer may be NULL to skip it.       */
+int race_get_matrix(const race_schedule *s, int32_t *row_ptr, int32_t *col, void *val);
+
+/* Copy the flattened phases: stage_ptr (n_phases+1) offsets into the leaf
+ * arrays; leaf_lo/leaf_hi (n_leaves) row ranges [lo, hi) in permuted order.*/
+int race_get_phases(const race_schedule *s, int32_t *stage_ptr, int32_t *leaf_lo, int32_t *leaf_hi);
+
+int race_get_info(const race_schedule *s, race_info *info);
+
+/* race_export — canonical byte image of the schedule (for bit-exact
+ * comparison and caching).  With buf == NULL, *size receives the needed
+ * size.  Layout (little-endian): int32 magic 0x45434152, version 1, n,
+ * n_workers, dist_k, balance, max_depth, n_nodes, n_phases, n_leaves, 0, 0;
+ * double eps[8], eta; int32 perm[n]; int32 stage_ptr[n_phases+1];
+ * n_leaves x (int32 lo, hi); then the tree in preorder, per node: int32
+ * stage, color, lo, hi, n_threads, thread_lo, n_levels_in_parent,
+ * n_sublevels, n_children, phase_count, phase_offset; int64 size, neff.    */
+int race_export(const race_schedule *s, void *buf, size_t *size);
+
+void race_free(race_schedule *s);
+const char *race_strerror(int code);
+const char *race_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RACE_GB300_H */

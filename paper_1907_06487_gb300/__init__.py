@@ -1,0 +1,265 @@
+"""RACE-scheduled symmetric SpMV for GB300 — Python binding of the C ABI.
+
+Argument marshalling only: every step of the path runs in the compiled
+library ``_build/librace_gb300.so`` (host schedule builder + sm_103a
+kernels).  There is no Python or CPU fallback: if the library is missing the
+import of ``lib()`` raises.
+
+Names follow the C ABI in ``include/race.h``:
+``race_build``, ``symm_spmv``, ``symm_spmm``, ``spmv_full``, ``race_permute``,
+``race_unpermute``, ``race_get_info``, ``race_export``, ``race_free``.
+Device arrays may be torch CUDA tensors (anything with ``data_ptr()``) or raw
+integer addresses; streams may be ``torch.cuda.Stream`` objects, raw handles
+or None (legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librace_gb300.so")
+
+RACE_OK = 0
+RACE_ERR_INVALID = 1
+RACE_ERR_OVERFLOW = 2
+RACE_ERR_NOMEM = 3
+RACE_ERR_CUDA = 4
+RACE_ERR_TIMEOUT = 5
+RACE_ERR_UNSUPPORTED = 6
+RACE_F64 = 0
+RACE_F32 = 1
+RACE_BAL_ROWS = 0
+RACE_BAL_NNZ = 1
+RACE_FLAG_HOST_ONLY = 1
+
+PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
+
+# every symbol include/race.h declares
+EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmm", "spmv_full", "race_prepare_full",
+            "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases",
+            "race_get_info", "race_export", "race_free", "race_strerror", "race_last_error_detail")
+
+
+class RaceError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        detail = ""
+        try:
+            detail = lib().race_last_error_detail().decode()
+        except Exception:  # pragma: no cover - detail is best effort
+            pass
+        msg = lib().race_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code}){': ' + detail if detail else ''}")
+
+
+class race_csr_upper(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("val_type", ctypes.c_int32)]
+
+
+class race_params(ctypes.Structure):
+    _fields_ = [("dist_k", ctypes.c_int32), ("n_workers", ctypes.c_int32), ("eps", ctypes.c_double * 8),
+                ("max_depth", ctypes.c_int32), ("balance", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class race_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz_upper", ctypes.c_int64), ("n_levels", ctypes.c_int32),
+                ("n_phases", ctypes.c_int32), ("n_leaves", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("n_workers", ctypes.c_int32), ("val_type", ctypes.c_int32),
+                ("group_lanes", ctypes.c_int32), ("eta", ctypes.c_double), ("neff_root", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} missing: run paper_1907_06487_gb300.build.build() first "
+                           "(there is no fallback path)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    L.race_default_params.argtypes = [ctypes.POINTER(race_params), i32]
+    L.race_default_params.restype = None
+    L.race_build.argtypes = [ctypes.POINTER(race_csr_upper), ctypes.POINTER(race_params), vp, ctypes.POINTER(vp)]
+    for name in ("symm_spmv", "spmv_full"):
+        getattr(L, name).argtypes = [vp, vp, vp, vp]
+    L.symm_spmm.argtypes = [vp, i32, vp, vp, vp]
+    L.race_prepare_full.argtypes = [vp, vp]
+    L.race_permute.argtypes = [vp, vp, vp, i32, vp]
+    L.race_unpermute.argtypes = [vp, vp, vp, i32, vp]
+    L.race_get_perm.argtypes = [vp, vp]
+    L.race_get_matrix.argtypes = [vp, vp, vp, vp]
+    L.race_get_phases.argtypes = [vp, vp, vp, vp]
+    L.race_get_info.argtypes = [vp, ctypes.POINTER(race_info)]
+    L.race_export.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.race_free.argtypes = [vp]
+    L.race_free.restype = None
+    L.race_strerror.argtypes = [ctypes.c_int]
+    L.race_strerror.restype = ctypes.c_char_p
+    L.race_last_error_detail.argtypes = []
+    L.race_last_error_detail.restype = ctypes.c_char_p
+    for name in ("race_build", "symm_spmv", "symm_spmm", "spmv_full", "race_prepare_full", "race_permute",
+                 "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases", "race_get_info",
+                 "race_export"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(f"cannot take a device pointer of {type(a)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, where):
+    if rc != RACE_OK:
+        raise RaceError(rc, where)
+
+
+def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False):
+    p = race_params()
+    lib().race_default_params(ctypes.byref(p), int(n_workers))
+    e = list(eps) + [eps[-1]] * (8 - len(eps))
+    for i in range(8):
+        p.eps[i] = float(e[i])
+    p.max_depth = int(max_depth)
+    p.balance = int(balance)
+    p.group_lanes = int(group_lanes)
+    p.flags = RACE_FLAG_HOST_ONLY if host_only else 0
+    return p
+
+
+class Schedule:
+    """Owns a ``race_schedule*``; freed by ``free()`` or garbage collection."""
+
+    def __init__(self, handle, n, k_hint=1):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("schedule already freed")
+        return self._h
+
+    def info(self):
+        inf = race_info()
+        _check(lib().race_get_info(self.handle, ctypes.byref(inf)), "race_get_info")
+        return inf.as_dict()
+
+    def export(self) -> bytes:
+        sz = ctypes.c_size_t(0)
+        _check(lib().race_export(self.handle, None, ctypes.byref(sz)), "race_export")
+        buf = (ctypes.c_uint8 * sz.value)()
+        _check(lib().race_export(self.handle, buf, ctypes.byref(sz)), "race_export")
+        return bytes(buf)
+
+    def perm(self):
+        out = np.zeros(self.n, np.int32)
+        _check(lib().race_get_perm(self.handle, out.ctypes.data), "race_get_perm")
+        return out
+
+    def matrix(self):
+        inf = self.info()
+        rp = np.zeros(self.n + 1, np.int32)
+        col = np.zeros(inf["nnz_upper"], np.int32)
+        val = np.zeros(inf["nnz_upper"], np.float64 if inf["val_type"] == RACE_F64 else np.float32)
+        _check(lib().race_get_matrix(self.handle, rp.ctypes.data, col.ctypes.data, val.ctypes.data),
+               "race_get_matrix")
+        return {"n": self.n, "row_ptr": rp, "col": col, "val": val}
+
+    def phases(self):
+        inf = self.info()
+        sp = np.zeros(inf["n_phases"] + 1, np.int32)
+        lo = np.zeros(inf["n_leaves"], np.int32)
+        hi = np.zeros(inf["n_leaves"], np.int32)
+        _check(lib().race_get_phases(self.handle, sp.ctypes.data, lo.ctypes.data, hi.ctypes.data), "race_get_phases")
+        return sp, lo, hi
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().race_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
+               host_only=False, stream=None, val_type=RACE_F64) -> Schedule:
+    """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
+    n = int(m["n"])
+    rp = np.ascontiguousarray(m["row_ptr"], dtype=np.int32)
+    col = np.ascontiguousarray(m["col"], dtype=np.int32)
+    val = np.ascontiguousarray(m["val"], dtype=np.float64 if val_type == RACE_F64 else np.float32)
+    a = race_csr_upper(n, int(rp[-1]) if n > 0 else 0, rp.ctypes.data, col.ctypes.data if len(col) else None,
+                       val.ctypes.data if len(val) else None, int(val_type))
+    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only)
+    h = ctypes.c_void_p()
+    _check(lib().race_build(ctypes.byref(a), ctypes.byref(p), _stream(stream), ctypes.byref(h)), "race_build")
+    return Schedule(h.value, n)
+
+
+def symm_spmv(s: Schedule, x, b, stream=None):
+    _check(lib().symm_spmv(s.handle, _ptr(x), _ptr(b), _stream(stream)), "symm_spmv")
+
+
+def symm_spmm(s: Schedule, k, X, B, stream=None):
+    _check(lib().symm_spmm(s.handle, int(k), _ptr(X), _ptr(B), _stream(stream)), "symm_spmm")
+
+
+def spmv_full(s: Schedule, x, b, stream=None):
+    _check(lib().spmv_full(s.handle, _ptr(x), _ptr(b), _stream(stream)), "spmv_full")
+
+
+def race_prepare_full(s: Schedule, stream=None):
+    _check(lib().race_prepare_full(s.handle, _stream(stream)), "race_prepare_full")
+
+
+def race_permute(s: Schedule, inp, out, k=1, stream=None):
+    _check(lib().race_permute(s.handle, _ptr(inp), _ptr(out), int(k), _stream(stream)), "race_permute")
+
+
+def race_unpermute(s: Schedule, inp, out, k=1, stream=None):
+    _check(lib().race_unpermute(s.handle, _ptr(inp), _ptr(out), int(k), _stream(stream)), "race_unpermute")
+
+
+def race_get_info(s: Schedule):
+    return s.info()
+
+
+def race_export(s: Schedule) -> bytes:
+    return s.export()
+
+
+def race_free(s: Schedule):
+    s.free()

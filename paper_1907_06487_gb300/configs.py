@@ -1,0 +1,52 @@
+"""Synthetic workloads shaped like the paper's benchmark matrices.
+
+Each workload is seeded and generated by ``matgen`` (the SuiteSparse/ScaMaC
+matrices of the paper's Table "Details of the benchmark matrices" are not
+available; these stand in for them):
+
+  anderson32  3D Anderson model 32^3 periodic (7-pt, hopping -1, disorder
+              U[-8.25, 8.25) seed 1), x ~ U[-1,1) seed 2   (paper: Anderson-16.5)
+  xxz26       periodic Heisenberg XXZ chain L=26, Sz=0 (10,400,600 rows,
+              J=1, Delta=1), x ~ U[-1,1) seed 3             (paper: Spin-26)
+  st27_200    3D 27-pt stencil 200^3 nonperiodic, off-diag -U(0,1] seed 4,
+              diag = row abs-sum + 1, X ~ U[-1,1) seed 5    (HPCG-like)
+
+``SCHEDULE`` holds the schedule parameters the benchmark and the full-size
+tests use for each workload.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import matgen
+
+SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
+
+# schedule parameters per workload: n_workers, eps, max_depth, executor
+SCHEDULE = {
+    "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1),
+    "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1),
+    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1),
+}
+
+
+def matrix(name: str) -> dict:
+    if name == "anderson32":
+        return matgen.anderson(32, W=16.5, seed=1)
+    if name == "xxz26":
+        return matgen.xxz(26, J=1.0, Delta=1.0)
+    if name == "st27_200":
+        return matgen.stencil3d(200, npt=27, seed=4)
+    if name.startswith("xxz"):
+        return matgen.xxz(int(name[3:]))
+    if name.startswith("anderson"):
+        return matgen.anderson(int(name[8:]), W=16.5, seed=1)
+    if name.startswith("st27_"):
+        return matgen.stencil3d(int(name[5:]), npt=27, seed=4)
+    raise KeyError(name)
+
+
+def vectors(name: str, n: int, k: int = 1) -> np.ndarray:
+    seed = SEEDS.get(name, (None, 7))[1]
+    x = matgen.uniform(n * k, seed, -1.0, 1.0)
+    return x if k == 1 else x.reshape(n, k)

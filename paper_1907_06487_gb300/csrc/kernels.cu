@@ -1,0 +1,450 @@
+// Device kernels and the compute entry points of the C ABI (sm_103a).
+//
+// SymmSpMV (Alg. "SymmSpMV"): each stored upper entry a_rc updates both
+// b[r] (row sum, gathered) and b[c] (scattered).  The RACE phases make the
+// scatter safe: leaves of one phase are distance-2 independent, so their
+// write sets {rows} U {upper columns of the rows} are disjoint and no two
+// concurrently running leaves touch the same entry of b.  One leaf runs on
+// one group of G lanes: rows in order, the lanes sharing the row's
+// nonzeros (the paper's SIMD-vectorised inner loop with VECWIDTH = G).
+// Because a phase's write sets are disjoint, b is read and written with
+// plain (non-atomic) loads and stores; the kernel boundary between phases
+// orders the phases.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "race_internal.h"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+template <int G>
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+
+template <typename VT>
+__device__ __forceinline__ double ldv(const VT* p) {
+    return static_cast<double>(__ldg(p));
+}
+
+// One phase of SymmSpMV: leaves [0, nleaf) of this phase.
+template <typename VT, int G>
+__global__ void __launch_bounds__(kBlock) k_symm_phase(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                      const VT* __restrict__ val, const double* __restrict__ x,
+                                                      double* b, const int32_t* __restrict__ llo,
+                                                      const int32_t* __restrict__ lhi, int32_t nleaf) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
+    for (int64_t q = gid; q < nleaf; q += ngroups) {
+        const int32_t lo = __ldg(llo + q), hi = __ldg(lhi + q);
+        int32_t rs = __ldg(rp + lo);
+        for (int32_t r = lo; r < hi; ++r) {
+            const int32_t re = __ldg(rp + r + 1);
+            const double xr = __ldg(x + r);
+            double tmp = 0.0;
+            for (int32_t idx = rs + lane; idx < re; idx += G) {
+                const double a = ldv(val + idx);
+                if (idx == rs) {
+                    tmp += a * xr;  // diagonal: first entry of the row
+                } else {
+                    const int32_t c = __ldg(col + idx);
+                    tmp += a * __ldg(x + c);
+                    b[c] += a * xr;
+                }
+            }
+            tmp = group_sum<G>(tmp, mask);
+            if (lane == 0) b[r] += tmp;
+            __syncwarp(mask);
+            rs = re;
+        }
+    }
+}
+
+// One phase of SymmSpMV with one CTA per leaf: the CTA's groups take the
+// leaf's rows round-robin; updates inside the leaf use reductions at L2
+// (red.global.add.f64).  Leaves of a phase are distance-2 independent, so no
+// two CTAs ever update the same entry of b.
+template <typename VT, int G>
+__global__ void __launch_bounds__(kBlock) k_symm_phase_cta(const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ col,
+                                                          const VT* __restrict__ val, const double* __restrict__ x,
+                                                          double* b, const int32_t* __restrict__ llo,
+                                                          const int32_t* __restrict__ lhi, int32_t nleaf) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int grp = threadIdx.x / G;
+    constexpr int kGroups = kBlock / G;
+    for (int64_t q = blockIdx.x; q < nleaf; q += gridDim.x) {
+        const int32_t lo = __ldg(llo + q), hi = __ldg(lhi + q);
+        for (int32_t r = lo + grp; r < hi; r += kGroups) {
+            const int32_t rs = __ldg(rp + r), re = __ldg(rp + r + 1);
+            const double xr = __ldg(x + r);
+            double tmp = 0.0;
+            for (int32_t idx = rs + lane; idx < re; idx += G) {
+                const double a = ldv(val + idx);
+                if (idx == rs) {
+                    tmp += a * xr;
+                } else {
+                    const int32_t c = __ldg(col + idx);
+                    tmp += a * __ldg(x + c);
+                    atomicAdd(b + c, a * xr);
+                }
+            }
+            tmp = group_sum<G>(tmp, mask);
+            if (lane == 0) atomicAdd(b + r, tmp);
+        }
+    }
+}
+
+// SymmSpMV without a schedule: all rows at once, every update a reduction
+// at L2.  A comparison point only (correct for any row order).
+template <typename VT, int G>
+__global__ void __launch_bounds__(kBlock) k_symm_atomic(int32_t n, const int32_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                       const double* __restrict__ x, double* b) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
+    for (int64_t r = gid; r < n; r += ngroups) {
+        const int32_t rs = __ldg(rp + r), re = __ldg(rp + r + 1);
+        const double xr = __ldg(x + r);
+        double tmp = 0.0;
+        for (int32_t idx = rs + lane; idx < re; idx += G) {
+            const double a = ldv(val + idx);
+            if (idx == rs) {
+                tmp += a * xr;
+            } else {
+                const int32_t c = __ldg(col + idx);
+                tmp += a * __ldg(x + c);
+                atomicAdd(b + c, a * xr);
+            }
+        }
+        tmp = group_sum<G>(tmp, mask);
+        if (lane == 0) atomicAdd(b + r, tmp);
+    }
+}
+
+// One phase of SymmSpMM with k right-hand sides (row-major n x k).  A warp
+// runs one leaf; lane l serves column l % K of nonzero slot l / K.
+template <typename VT, int K>
+__global__ void __launch_bounds__(kBlock) k_symm_mm_phase(const int32_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                         const double* __restrict__ X, double* B,
+                                                         const int32_t* __restrict__ llo,
+                                                         const int32_t* __restrict__ lhi, int32_t nleaf) {
+    constexpr int S = 32 / K;  // nonzero slots per warp
+    const int lane = threadIdx.x & 31;
+    const int c = lane % K, slot = lane / K;
+    const int64_t wid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / 32;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kBlock / 32;
+    for (int64_t q = wid; q < nleaf; q += nwarps) {
+        const int32_t lo = __ldg(llo + q), hi = __ldg(lhi + q);
+        int32_t rs = __ldg(rp + lo);
+        for (int32_t r = lo; r < hi; ++r) {
+            const int32_t re = __ldg(rp + r + 1);
+            const double xr = __ldg(X + static_cast<int64_t>(r) * K + c);
+            double tmp = 0.0;
+            for (int32_t idx = rs + slot; idx < re; idx += S) {
+                const double a = ldv(val + idx);
+                if (idx == rs) {
+                    tmp += a * xr;
+                } else {
+                    const int64_t cc = __ldg(col + idx);
+                    tmp += a * __ldg(X + cc * K + c);
+                    B[cc * K + c] += a * xr;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= K; o >>= 1) tmp += __shfl_xor_sync(0xffffffffu, tmp, o);
+            if (slot == 0) B[static_cast<int64_t>(r) * K + c] += tmp;
+            __syncwarp();
+            rs = re;
+        }
+    }
+}
+
+// Alg. "SpMV using the CRS format" on the full matrix, G lanes per row.
+template <typename VT, int G>
+__global__ void __launch_bounds__(kBlock) k_spmv_full(int32_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                     const double* __restrict__ x, double* __restrict__ b) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
+    for (int64_t r = gid; r < n; r += ngroups) {
+        const int32_t rs = __ldg(rp + r), re = __ldg(rp + r + 1);
+        double tmp = 0.0;
+        for (int32_t idx = rs + lane; idx < re; idx += G) tmp += ldv(val + idx) * __ldg(x + __ldg(col + idx));
+        tmp = group_sum<G>(tmp, mask);
+        if (lane == 0) b[r] = tmp;
+    }
+}
+
+__global__ void k_permute(int32_t n, int32_t k, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                          double* __restrict__ out, int inverse) {
+    const int64_t total = static_cast<int64_t>(n) * k;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t q = t / k, c = t % k;
+        const int64_t o = __ldg(perm + q);
+        if (inverse) out[o * k + c] = in[t];
+        else out[t] = in[o * k + c];
+    }
+}
+
+int g_sm_count = 0;
+int sm_count() {
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+    }
+    return g_sm_count;
+}
+
+int grid_for(int64_t threads_needed) {
+    const int64_t cap = static_cast<int64_t>(sm_count()) * (2048 / kBlock);
+    int64_t blocks = (threads_needed + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min(blocks, cap)));
+}
+
+int check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        race_set_detail(std::string(what) + ": " + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    return RACE_OK;
+}
+
+template <typename VT, int G>
+void launch_phases(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const auto& sp = s->plan.stage_ptr;
+    const VT* val = static_cast<const VT*>(s->d_val);
+    for (size_t p = 0; p + 1 < sp.size(); ++p) {
+        const int32_t nl = sp[p + 1] - sp[p];
+        if (nl == 0) continue;
+        k_symm_phase<VT, G><<<grid_for(static_cast<int64_t>(nl) * G), kBlock, 0, st>>>(
+            s->d_rp, s->d_col, val, x, b, s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
+    }
+}
+
+template <typename VT, int G>
+void launch_phases_cta(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const auto& sp = s->plan.stage_ptr;
+    const VT* val = static_cast<const VT*>(s->d_val);
+    const int cap = sm_count() * (2048 / kBlock);
+    for (size_t p = 0; p + 1 < sp.size(); ++p) {
+        const int32_t nl = sp[p + 1] - sp[p];
+        if (nl == 0) continue;
+        k_symm_phase_cta<VT, G><<<std::min(nl, cap), kBlock, 0, st>>>(s->d_rp, s->d_col, val, x, b,
+                                                                       s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
+    }
+}
+
+template <typename VT, int G>
+void launch_atomic(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const int32_t n = s->plan.n;
+    k_symm_atomic<VT, G><<<grid_for(static_cast<int64_t>(n) * G), kBlock, 0, st>>>(
+        n, s->d_rp, s->d_col, static_cast<const VT*>(s->d_val), x, b);
+}
+
+template <typename VT>
+void launch_symm_exec(const race_schedule* s, int exec, const double* x, double* b, cudaStream_t st) {
+#define RACE_DISPATCH(FN)                          \
+    switch (s->group_lanes) {                      \
+        case 4: FN<VT, 4>(s, x, b, st); break;     \
+        case 8: FN<VT, 8>(s, x, b, st); break;     \
+        case 16: FN<VT, 16>(s, x, b, st); break;   \
+        default: FN<VT, 32>(s, x, b, st); break;   \
+    }
+    if (exec == RACE_EXEC_LEAF_CTA) {
+        RACE_DISPATCH(launch_phases_cta)
+    } else if (exec == RACE_EXEC_ATOMIC) {
+        RACE_DISPATCH(launch_atomic)
+    } else {
+        RACE_DISPATCH(launch_phases)
+    }
+#undef RACE_DISPATCH
+}
+
+template <typename VT>
+void launch_symm(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    switch (s->group_lanes) {
+        case 4: launch_phases<VT, 4>(s, x, b, st); break;
+        case 8: launch_phases<VT, 8>(s, x, b, st); break;
+        case 16: launch_phases<VT, 16>(s, x, b, st); break;
+        default: launch_phases<VT, 32>(s, x, b, st); break;
+    }
+}
+
+template <typename VT, int K>
+void launch_mm(const race_schedule* s, const double* X, double* B, cudaStream_t st) {
+    const auto& sp = s->plan.stage_ptr;
+    const VT* val = static_cast<const VT*>(s->d_val);
+    for (size_t p = 0; p + 1 < sp.size(); ++p) {
+        const int32_t nl = sp[p + 1] - sp[p];
+        if (nl == 0) continue;
+        k_symm_mm_phase<VT, K><<<grid_for(static_cast<int64_t>(nl) * 32), kBlock, 0, st>>>(
+            s->d_rp, s->d_col, val, X, B, s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
+    }
+}
+
+template <typename VT>
+int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, cudaStream_t st) {
+    switch (k) {
+        case 1: launch_mm<VT, 1>(s, X, B, st); break;
+        case 2: launch_mm<VT, 2>(s, X, B, st); break;
+        case 4: launch_mm<VT, 4>(s, X, B, st); break;
+        case 8: launch_mm<VT, 8>(s, X, B, st); break;
+        case 16: launch_mm<VT, 16>(s, X, B, st); break;
+        default: return RACE_ERR_UNSUPPORTED;
+    }
+    return RACE_OK;
+}
+
+template <typename VT, int G>
+void launch_full_g(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const int32_t n = s->plan.n;
+    k_spmv_full<VT, G><<<grid_for(static_cast<int64_t>(n) * G), kBlock, 0, st>>>(
+        n, s->d_frp, s->d_fcol, static_cast<const VT*>(s->d_fval), x, b);
+}
+
+template <typename VT>
+void launch_full(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    switch (s->full_lanes) {
+        case 4: launch_full_g<VT, 4>(s, x, b, st); break;
+        case 8: launch_full_g<VT, 8>(s, x, b, st); break;
+        case 16: launch_full_g<VT, 16>(s, x, b, st); break;
+        default: launch_full_g<VT, 32>(s, x, b, st); break;
+    }
+}
+
+int precheck(const race_schedule* s, const void* a, const void* b) {
+    if (!s || !a || !b) {
+        race_set_detail("NULL argument");
+        return RACE_ERR_INVALID;
+    }
+    if (s->host_only) {
+        race_set_detail("schedule was built with RACE_FLAG_HOST_ONLY");
+        return RACE_ERR_UNSUPPORTED;
+    }
+    if (a == b) {
+        race_set_detail("input and output alias");
+        return RACE_ERR_INVALID;
+    }
+    return RACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stream) {
+    int rc = precheck(s, x_d, b_d);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b_d, 0, sizeof(double) * static_cast<size_t>(s->plan.n), st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("memset: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    if (s->val_type == RACE_F64) launch_symm<double>(s, x_d, b_d, st);
+    else launch_symm<float>(s, x_d, b_d, st);
+    return check_launch("symm_spmv");
+}
+
+int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
+    int rc = precheck(s, x_d, b_d);
+    if (rc) return rc;
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_ATOMIC) {
+        race_set_detail("unknown executor");
+        return RACE_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b_d, 0, sizeof(double) * static_cast<size_t>(s->plan.n), st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("memset: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    if (s->val_type == RACE_F64) launch_symm_exec<double>(s, executor, x_d, b_d, st);
+    else launch_symm_exec<float>(s, executor, x_d, b_d, st);
+    return check_launch("symm_spmv_exec");
+}
+
+int symm_spmm(const race_schedule* s, int32_t k, const double* X_d, double* B_d, void* stream) {
+    int rc = precheck(s, X_d, B_d);
+    if (rc) return rc;
+    if (k < 1 || k > 16) {
+        race_set_detail("k must be in 1..16");
+        return RACE_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(B_d, 0, sizeof(double) * static_cast<size_t>(s->plan.n) * k, st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("memset: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    rc = s->val_type == RACE_F64 ? launch_mm_k<double>(s, k, X_d, B_d, st) : launch_mm_k<float>(s, k, X_d, B_d, st);
+    if (rc) {
+        race_set_detail("k must be 1, 2, 4, 8 or 16");
+        return rc;
+    }
+    return check_launch("symm_spmm");
+}
+
+int spmv_full(const race_schedule* s, const double* x_d, double* b_d, void* stream) {
+    int rc = precheck(s, x_d, b_d);
+    if (rc) return rc;
+    if (!s->d_frp) {
+        rc = race_prepare_full(const_cast<race_schedule*>(s), stream);
+        if (rc) return rc;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->val_type == RACE_F64) launch_full<double>(s, x_d, b_d, st);
+    else launch_full<float>(s, x_d, b_d, st);
+    return check_launch("spmv_full");
+}
+
+static int permute_impl(const race_schedule* s, const double* in, double* out, int32_t k, void* stream, int inv) {
+    int rc = precheck(s, in, out);
+    if (rc) return rc;
+    if (k < 1) {
+        race_set_detail("k < 1");
+        return RACE_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_permute<<<grid_for(static_cast<int64_t>(s->plan.n) * k), kBlock, 0, st>>>(s->plan.n, k, s->d_perm, in, out, inv);
+    return check_launch("race_permute");
+}
+
+int race_permute(const race_schedule* s, const double* in_d, double* out_d, int32_t k, void* stream) {
+    return permute_impl(s, in_d, out_d, k, stream, 0);
+}
+
+int race_unpermute(const race_schedule* s, const double* in_d, double* out_d, int32_t k, void* stream) {
+    return permute_impl(s, in_d, out_d, k, stream, 1);
+}
+
+}  // extern "C"

@@ -1,0 +1,360 @@
+// Host side of the C ABI: input validation and canonicalisation, the
+// symmetric permutation of the upper CRS, device upload, export, getters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "race_internal.h"
+
+namespace {
+thread_local std::string g_detail;
+
+int fail(int code, const std::string& why) {
+    g_detail = why;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_detail = std::string(what) + ": " + cudaGetErrorString(e);
+    return RACE_ERR_CUDA;
+}
+
+void release_device(race_schedule* s) {
+    void* ptrs[] = {s->d_rp, s->d_col, s->d_val, s->d_leaf_lo, s->d_leaf_hi, s->d_perm,
+                    s->d_frp, s->d_fcol, s->d_fval};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
+    s->d_val = s->d_fval = nullptr;
+}
+
+template <typename T>
+int upload(const std::vector<T>& h, T** d, cudaStream_t st) {
+    const size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d), bytes);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(RACE_ERR_NOMEM, "cudaMalloc") : cuda_fail(e, "cudaMalloc");
+    if (!h.empty()) {
+        e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    return RACE_OK;
+}
+
+// Canonical rows: diagonal first, strictly increasing columns, explicit 0.0
+// diagonal when the input has none (the diagonal is the first entry of each
+// row in Alg. "SymmSpMV").  Values kept in double here.
+int canonicalize(const race_csr_upper* a, std::vector<int32_t>& rp, std::vector<int32_t>& col,
+                 std::vector<double>& val) {
+    const int32_t n = a->n;
+    if (a->row_ptr[0] != 0) return fail(RACE_ERR_INVALID, "row_ptr[0] != 0");
+    if (static_cast<int64_t>(a->row_ptr[n]) != a->nnz) return fail(RACE_ERR_INVALID, "row_ptr[n] != nnz");
+    for (int32_t i = 0; i < n; ++i)
+        if (a->row_ptr[i + 1] < a->row_ptr[i]) return fail(RACE_ERR_INVALID, "row_ptr not monotone");
+    rp.assign(static_cast<size_t>(n) + 1, 0);
+    col.clear();
+    val.clear();
+    col.reserve(static_cast<size_t>(a->nnz) + n);
+    val.reserve(static_cast<size_t>(a->nnz) + n);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int32_t i = 0; i < n; ++i) {
+        row.clear();
+        bool diag = false;
+        for (int64_t t = a->row_ptr[i]; t < a->row_ptr[i + 1]; ++t) {
+            const int32_t c = a->col[t];
+            if (c < i || c >= n) return fail(RACE_ERR_INVALID, "column below the diagonal or out of range in row " + std::to_string(i));
+            const double v = a->val_type == RACE_F32 ? static_cast<double>(static_cast<const float*>(a->val)[t])
+                                                     : static_cast<const double*>(a->val)[t];
+            if (!std::isfinite(v)) return fail(RACE_ERR_INVALID, "non-finite value in row " + std::to_string(i));
+            diag |= (c == i);
+            row.push_back({c, t});
+        }
+        std::sort(row.begin(), row.end());
+        for (size_t q = 1; q < row.size(); ++q)
+            if (row[q].first == row[q - 1].first) return fail(RACE_ERR_INVALID, "duplicate column in row " + std::to_string(i));
+        if (!diag) {
+            col.push_back(i);
+            val.push_back(0.0);
+        }
+        for (auto& e : row) {
+            col.push_back(e.first);
+            val.push_back(a->val_type == RACE_F32 ? static_cast<double>(static_cast<const float*>(a->val)[e.second])
+                                                  : static_cast<const double*>(a->val)[e.second]);
+        }
+        if (col.size() >= static_cast<size_t>(INT32_MAX)) return fail(RACE_ERR_OVERFLOW, "nnz >= 2^31");
+        rp[i + 1] = static_cast<int32_t>(col.size());
+    }
+    return RACE_OK;
+}
+
+// Upper CRS of P A P^T: the entry (i, j) moves to row min(P i, P j),
+// column max(P i, P j); each row sorted by column (diagonal first).
+void permute_upper(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                   const std::vector<double>& val, const std::vector<int32_t>& perm, std::vector<int32_t>& prp,
+                   std::vector<int32_t>& pcol, std::vector<double>& pval) {
+    std::vector<int32_t> where(n);
+    for (int32_t q = 0; q < n; ++q) where[perm[q]] = q;
+    prp.assign(static_cast<size_t>(n) + 1, 0);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) ++prp[std::min(where[i], where[col[t]]) + 1];
+    for (int32_t i = 0; i < n; ++i) prp[i + 1] += prp[i];
+    std::vector<std::pair<int32_t, double>> tmp(col.size());
+    std::vector<int32_t> fill(prp.begin(), prp.end() - 1);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            const int32_t u = where[i], w = where[col[t]];
+            tmp[fill[std::min(u, w)]++] = {std::max(u, w), val[t]};
+        }
+    for (int32_t r = 0; r < n; ++r)
+        std::sort(tmp.begin() + prp[r], tmp.begin() + prp[r + 1],
+                  [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
+    pcol.resize(col.size());
+    pval.resize(col.size());
+    for (size_t q = 0; q < tmp.size(); ++q) {
+        pcol[q] = tmp[q].first;
+        pval[q] = tmp[q].second;
+    }
+}
+
+int pick_lanes(int64_t nnz, int32_t n) {
+    const double per_row = n > 0 ? static_cast<double>(nnz) / n : 1.0;
+    if (per_row <= 4.5) return 4;
+    if (per_row <= 9.0) return 8;
+    if (per_row <= 18.0) return 16;
+    return 32;
+}
+}  // namespace
+
+void race_set_detail(const std::string& s) { g_detail = s; }
+
+extern "C" {
+
+void race_default_params(race_params* p, int32_t n_workers) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dist_k = 2;
+    p->n_workers = n_workers;
+    p->eps[0] = 0.8;
+    p->eps[1] = 0.8;
+    for (int i = 2; i < 8; ++i) p->eps[i] = 0.5;
+    p->max_depth = -1;
+    p->balance = RACE_BAL_ROWS;
+    p->group_lanes = 0;
+    p->flags = 0;
+}
+
+int race_build(const race_csr_upper* a, const race_params* p, void* stream, race_schedule** out) {
+    if (!out) return fail(RACE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!a || !p) return fail(RACE_ERR_INVALID, "NULL argument");
+    if (a->n <= 0) return fail(RACE_ERR_INVALID, "n <= 0");
+    if (a->nnz < 0 || (a->nnz > 0 && (!a->col || !a->val)) || !a->row_ptr) return fail(RACE_ERR_INVALID, "NULL matrix array");
+    if (a->nnz + a->n >= static_cast<int64_t>(INT32_MAX)) return fail(RACE_ERR_OVERFLOW, "nnz + n >= 2^31");
+    if (a->val_type != RACE_F64 && a->val_type != RACE_F32) return fail(RACE_ERR_INVALID, "val_type");
+    if (p->dist_k != 2) return fail(RACE_ERR_UNSUPPORTED, "only distance-2 colouring (SymmSpMV) is built");
+    if (p->n_workers < 1) return fail(RACE_ERR_INVALID, "n_workers < 1");
+    for (int i = 0; i < 8; ++i)
+        if (!(p->eps[i] >= 0.5 && p->eps[i] < 1.0)) return fail(RACE_ERR_INVALID, "eps_s outside [0.5, 1)");
+    if (p->balance != RACE_BAL_ROWS && p->balance != RACE_BAL_NNZ) return fail(RACE_ERR_INVALID, "balance");
+    if (p->group_lanes != 0 && p->group_lanes != 4 && p->group_lanes != 8 && p->group_lanes != 16 && p->group_lanes != 32)
+        return fail(RACE_ERR_INVALID, "group_lanes must be 0, 4, 8, 16 or 32");
+
+    race_schedule* s = new (std::nothrow) race_schedule();
+    if (!s) return fail(RACE_ERR_NOMEM, "host allocation");
+    int rc = RACE_OK;
+    try {
+        std::vector<int32_t> rp, col;
+        std::vector<double> val;
+        rc = canonicalize(a, rp, col, val);
+        if (rc != RACE_OK) {
+            delete s;
+            return rc;
+        }
+        race::build_plan(a->n, rp.data(), col.data(), *p, s->plan);
+        permute_upper(a->n, rp, col, val, s->plan.perm, s->h_rp, s->h_col, s->h_val64);
+        s->val_type = a->val_type;
+        if (a->val_type == RACE_F32) {
+            s->h_val32.assign(s->h_val64.begin(), s->h_val64.end());
+            std::vector<double>().swap(s->h_val64);
+        }
+        s->group_lanes = p->group_lanes ? p->group_lanes : pick_lanes(static_cast<int64_t>(s->h_col.size()), a->n);
+        s->host_only = (p->flags & RACE_FLAG_HOST_ONLY) ? 1 : 0;
+    } catch (const std::bad_alloc&) {
+        delete s;
+        return fail(RACE_ERR_NOMEM, "host allocation during build");
+    }
+    if (!s->host_only) {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        cudaGetDevice(&s->device);
+        if ((rc = upload(s->h_rp, &s->d_rp, st)) || (rc = upload(s->h_col, &s->d_col, st)) ||
+            (rc = upload(s->plan.leaf_lo, &s->d_leaf_lo, st)) || (rc = upload(s->plan.leaf_hi, &s->d_leaf_hi, st)) ||
+            (rc = upload(s->plan.perm, &s->d_perm, st))) {
+            release_device(s);
+            delete s;
+            return rc;
+        }
+        if (s->val_type == RACE_F64) {
+            double* d = nullptr;
+            rc = upload(s->h_val64, &d, st);
+            s->d_val = d;
+        } else {
+            float* d = nullptr;
+            rc = upload(s->h_val32, &d, st);
+            s->d_val = d;
+        }
+        if (rc == RACE_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "upload");
+        }
+        if (rc != RACE_OK) {
+            release_device(s);
+            delete s;
+            return rc;
+        }
+    }
+    *out = s;
+    return RACE_OK;
+}
+
+int race_prepare_full(race_schedule* s, void* stream) {
+    if (!s) return fail(RACE_ERR_INVALID, "NULL schedule");
+    if (s->host_only) return fail(RACE_ERR_UNSUPPORTED, "host-only schedule");
+    if (s->d_frp) return RACE_OK;
+    const int32_t n = s->plan.n;
+    const int64_t nnz_full = 2 * static_cast<int64_t>(s->h_col.size()) - n;
+    if (nnz_full >= INT32_MAX) return fail(RACE_ERR_OVERFLOW, "full nnz >= 2^31");
+    std::vector<int32_t> frp(static_cast<size_t>(n) + 1, 0), fcol(static_cast<size_t>(nnz_full));
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = s->h_rp[r]; t < s->h_rp[r + 1]; ++t) {
+            ++frp[r + 1];
+            if (s->h_col[t] != r) ++frp[s->h_col[t] + 1];
+        }
+    for (int32_t r = 0; r < n; ++r) frp[r + 1] += frp[r];
+    std::vector<int32_t> fill(frp.begin(), frp.end() - 1);
+    std::vector<double> fval64;
+    std::vector<float> fval32;
+    if (s->val_type == RACE_F64) fval64.resize(static_cast<size_t>(nnz_full));
+    else fval32.resize(static_cast<size_t>(nnz_full));
+    auto put = [&](int32_t row, int32_t c, int32_t t) {
+        const int32_t q = fill[row]++;
+        fcol[q] = c;
+        if (s->val_type == RACE_F64) fval64[q] = s->h_val64[t];
+        else fval32[q] = s->h_val32[t];
+    };
+    // lower part first (rows r < c in increasing order), then the upper part,
+    // so every full row is sorted by column
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = s->h_rp[r] + 1; t < s->h_rp[r + 1]; ++t) put(s->h_col[t], r, t);
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = s->h_rp[r]; t < s->h_rp[r + 1]; ++t) put(r, s->h_col[t], t);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload(frp, &s->d_frp, st);
+    if (rc == RACE_OK) rc = upload(fcol, &s->d_fcol, st);
+    if (rc == RACE_OK) {
+        if (s->val_type == RACE_F64) {
+            double* d = nullptr;
+            rc = upload(fval64, &d, st);
+            s->d_fval = d;
+        } else {
+            float* d = nullptr;
+            rc = upload(fval32, &d, st);
+            s->d_fval = d;
+        }
+    }
+    if (rc == RACE_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "full upload");
+    }
+    s->nnz_full = nnz_full;
+    const double per_row = static_cast<double>(nnz_full) / n;
+    s->full_lanes = per_row <= 4.5 ? 4 : per_row <= 9.0 ? 8 : per_row <= 18.0 ? 16 : 32;
+    return rc;
+}
+
+int race_get_perm(const race_schedule* s, int32_t* perm_host) {
+    if (!s || !perm_host) return fail(RACE_ERR_INVALID, "NULL argument");
+    std::memcpy(perm_host, s->plan.perm.data(), sizeof(int32_t) * s->plan.perm.size());
+    return RACE_OK;
+}
+
+int race_get_matrix(const race_schedule* s, int32_t* row_ptr, int32_t* col, void* val) {
+    if (!s) return fail(RACE_ERR_INVALID, "NULL schedule");
+    if (row_ptr) std::memcpy(row_ptr, s->h_rp.data(), sizeof(int32_t) * s->h_rp.size());
+    if (col) std::memcpy(col, s->h_col.data(), sizeof(int32_t) * s->h_col.size());
+    if (val) {
+        if (s->val_type == RACE_F64) std::memcpy(val, s->h_val64.data(), sizeof(double) * s->h_val64.size());
+        else std::memcpy(val, s->h_val32.data(), sizeof(float) * s->h_val32.size());
+    }
+    return RACE_OK;
+}
+
+int race_get_phases(const race_schedule* s, int32_t* stage_ptr, int32_t* leaf_lo, int32_t* leaf_hi) {
+    if (!s) return fail(RACE_ERR_INVALID, "NULL schedule");
+    if (stage_ptr) std::memcpy(stage_ptr, s->plan.stage_ptr.data(), sizeof(int32_t) * s->plan.stage_ptr.size());
+    if (leaf_lo) std::memcpy(leaf_lo, s->plan.leaf_lo.data(), sizeof(int32_t) * s->plan.leaf_lo.size());
+    if (leaf_hi) std::memcpy(leaf_hi, s->plan.leaf_hi.data(), sizeof(int32_t) * s->plan.leaf_hi.size());
+    return RACE_OK;
+}
+
+int race_get_info(const race_schedule* s, race_info* info) {
+    if (!s || !info) return fail(RACE_ERR_INVALID, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n = s->plan.n;
+    info->nnz_upper = static_cast<int64_t>(s->h_col.size());
+    info->n_levels = s->plan.n_levels;
+    info->n_phases = static_cast<int32_t>(s->plan.stage_ptr.size()) - 1;
+    info->n_leaves = static_cast<int32_t>(s->plan.leaf_lo.size());
+    info->n_nodes = static_cast<int32_t>(s->plan.nodes.size());
+    int32_t depth = 0;
+    for (const auto& t : s->plan.nodes) depth = std::max(depth, t.stage + 1);
+    info->depth = depth;
+    info->n_workers = s->plan.n_workers;
+    info->val_type = s->val_type;
+    info->group_lanes = s->group_lanes;
+    info->eta = s->plan.eta;
+    info->neff_root = s->plan.nodes[0].neff;
+    return RACE_OK;
+}
+
+int race_export(const race_schedule* s, void* buf, size_t* size) {
+    if (!s || !size) return fail(RACE_ERR_INVALID, "NULL argument");
+    std::vector<uint8_t> img = race::export_plan(s->plan);
+    if (!buf) {
+        *size = img.size();
+        return RACE_OK;
+    }
+    if (*size < img.size()) {
+        *size = img.size();
+        return fail(RACE_ERR_INVALID, "export buffer too small");
+    }
+    std::memcpy(buf, img.data(), img.size());
+    *size = img.size();
+    return RACE_OK;
+}
+
+void race_free(race_schedule* s) {
+    if (!s) return;
+    release_device(s);
+    delete s;
+}
+
+const char* race_strerror(int code) {
+    switch (code) {
+        case RACE_OK: return "ok";
+        case RACE_ERR_INVALID: return "invalid argument or malformed matrix";
+        case RACE_ERR_OVERFLOW: return "size exceeds the int32 layout";
+        case RACE_ERR_NOMEM: return "out of memory";
+        case RACE_ERR_CUDA: return "CUDA runtime error";
+        case RACE_ERR_TIMEOUT: return "bounded device wait gave up";
+        case RACE_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown error code";
+    }
+}
+
+const char* race_last_error_detail(void) { return g_detail.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/race.h"
+
+namespace race {
+
+// One node of the RACE tree (Sec. 4.4.3, tree of Fig. "internal tree").
+struct TreeNode {
+    int32_t stage = -1;       // s of T_s(i); the root T_{-1}(0) has -1
+    int32_t color = 0;        // 0 red, 1 blue
+    int32_t lo = 0, hi = 0;   // rows [lo, hi) in the final permuted order
+    int32_t n_threads = 1;    // n_t(T_s(i))
+    int32_t thread_lo = 0;    // first thread id (ids are consecutive)
+    int32_t n_levels = 0;     // parent levels spanned by this group
+    int32_t n_sub = 0;        // own levels when it was split (0 = not split)
+    int32_t phase_count = 1;
+    int32_t phase_off = 0;
+    int64_t size = 0;         // rows (or nnz weight) of the group
+    int64_t neff = 0;         // effective row count (Sec. 5)
+    std::vector<int32_t> kids;
+};
+
+// Host-side result of the schedule construction.
+struct Plan {
+    int32_t n = 0, n_workers = 1, dist_k = 2, balance = 0, max_depth = -1;
+    double eps[8] = {0};
+    int32_t n_levels = 0;                  // BFS levels of the whole graph
+    std::vector<int32_t> perm;             // perm[new] = old
+    std::vector<TreeNode> nodes;           // nodes[0] = root
+    std::vector<int32_t> stage_ptr;        // n_phases + 1
+    std::vector<int32_t> leaf_lo, leaf_hi; // flattened non-empty leaves
+    double eta = 0.0;
+};
+
+// Builds the RACE plan for the symmetric graph given by an upper CRS whose
+// rows are canonical (diagonal first, strictly increasing columns).
+void build_plan(int32_t n, const int32_t* row_ptr, const int32_t* col, const race_params& p, Plan& out);
+
+// Canonical export image (layout documented in race.h).
+std::vector<uint8_t> export_plan(const Plan& plan);
+
+}  // namespace race
+
+// The opaque handle of the C ABI.
+struct race_schedule {
+    race::Plan plan;
+    int32_t val_type = RACE_F64;
+    int32_t group_lanes = 8;
+    int32_t host_only = 0;
+    // permuted upper CRS, host copies
+    std::vector<int32_t> h_rp, h_col;
+    std::vector<double> h_val64;
+    std::vector<float> h_val32;
+    // device copies
+    int32_t* d_rp = nullptr;
+    int32_t* d_col = nullptr;
+    void* d_val = nullptr;
+    int32_t* d_leaf_lo = nullptr;
+    int32_t* d_leaf_hi = nullptr;
+    int32_t* d_perm = nullptr;
+    // full CRS for the spmv_full baseline (lazy)
+    int32_t* d_frp = nullptr;
+    int32_t* d_fcol = nullptr;
+    void* d_fval = nullptr;
+    int64_t nnz_full = 0;
+    int32_t full_lanes = 8;
+    int32_t device = 0;
+};
+
+// Error detail for race_last_error_detail (thread-local).
+void race_set_detail(const std::string& s);
