@@ -38,7 +38,7 @@ RACE_FLAG_HOST_ONLY = 1
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
 # every symbol include/race.h declares
-EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmm", "spmv_full", "race_prepare_full",
+EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full", "race_prepare_full",
             "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases",
             "race_get_info", "race_export", "race_free", "race_strerror", "race_last_error_detail")
 
@@ -95,6 +95,7 @@ def lib():
     for name in ("symm_spmv", "spmv_full"):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.symm_spmm.argtypes = [vp, i32, vp, vp, vp]
+    L.symm_spmv_exec.argtypes = [vp, i32, vp, vp, vp]
     L.race_prepare_full.argtypes = [vp, vp]
     L.race_permute.argtypes = [vp, vp, vp, i32, vp]
     L.race_unpermute.argtypes = [vp, vp, vp, i32, vp]
@@ -109,7 +110,7 @@ def lib():
     L.race_strerror.restype = ctypes.c_char_p
     L.race_last_error_detail.argtypes = []
     L.race_last_error_detail.restype = ctypes.c_char_p
-    for name in ("race_build", "symm_spmv", "symm_spmm", "spmv_full", "race_prepare_full", "race_permute",
+    for name in ("race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full", "race_prepare_full", "race_permute",
                  "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases", "race_get_info",
                  "race_export"):
         getattr(L, name).restype = ctypes.c_int
@@ -231,6 +232,10 @@ def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS,
 
 def symm_spmv(s: Schedule, x, b, stream=None):
     _check(lib().symm_spmv(s.handle, _ptr(x), _ptr(b), _stream(stream)), "symm_spmv")
+
+
+def symm_spmv_exec(s: Schedule, executor, x, b, stream=None):
+    _check(lib().symm_spmv_exec(s.handle, int(executor), _ptr(x), _ptr(b), _stream(stream)), "symm_spmv_exec")
 
 
 def symm_spmm(s: Schedule, k, X, B, stream=None):

@@ -36,7 +36,7 @@ def run_symm(s, m, x, dev, executor=None):
     if executor is None:
         R.symm_spmv(s, xd, bd)
     else:
-        assert R.lib().symm_spmv_exec(s.handle, executor, xd.data_ptr(), bd.data_ptr(), None) == 0
+        R.symm_spmv_exec(s, executor, xd, bd)
     torch.cuda.synchronize()
     b = np.empty_like(x)
     b[perm] = bd.cpu().numpy()

@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
     assert len(names) >= 16
     for n in names:
         assert hasattr(lib, n), n
-    assert set(names) <= set(R.EXPORTED) | {"symm_spmv_exec"}
+    assert set(names) == set(R.EXPORTED)
 
 
 def test_strerror(lib):
