@@ -137,6 +137,25 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
 #define RACE_EXEC_ATOMIC     2  /* comparison point: no phases, every update
                                    a reduction at L2 (ignores the schedule)  */
 
+#define RACE_EXEC_ROWS_RED   3  /* all rows at once in row blocks (streamed,
+                                   coalesced); the transposed part and the row
+                                   sums are reductions at L2 on the permuted
+                                   matrix                                   */
+
+/* Launch shape of a kernel family; set by an autotuner or by hand.          */
+typedef struct {
+    int32_t executor;        /* RACE_EXEC_* (symm_spmv only)                */
+    int32_t group_lanes;     /* lanes per row group: 4, 8, 16 or 32         */
+    int32_t rows_per_group;  /* consecutive rows a group streams: 1,2,4,8
+                                (RACE_EXEC_ROWS_RED and spmv_full)          */
+    int32_t blocks_per_sm;   /* resident 256-thread blocks per SM, 0 = max  */
+} race_launch;
+
+/* race_set_launch / race_get_launch — which = 0: symm_spmv, which = 1:
+ * spmv_full.  Out-of-range shapes return RACE_ERR_INVALID.                 */
+int race_set_launch(race_schedule *s, int32_t which, const race_launch *l);
+int race_get_launch(const race_schedule *s, int32_t which, race_launch *l);
+
 /* symm_spmv_exec — symm_spmv with an explicit executor (RACE_EXEC_*).
  * Same arguments, layout and errors as symm_spmv.                          */
 int symm_spmv_exec(const race_schedule *s, int32_t executor, const double *x_d, double *b_d, void *stream);

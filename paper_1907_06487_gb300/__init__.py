@@ -38,9 +38,20 @@ RACE_FLAG_HOST_ONLY = 1
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
 # every symbol include/race.h declares
-EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full", "race_prepare_full",
-            "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases",
-            "race_get_info", "race_export", "race_free", "race_strerror", "race_last_error_detail")
+EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full",
+            "race_prepare_full", "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix",
+            "race_get_phases", "race_get_info", "race_export", "race_free", "race_strerror",
+            "race_last_error_detail", "race_set_launch", "race_get_launch")
+
+RACE_EXEC_LEAF_GROUP = 0
+RACE_EXEC_LEAF_CTA = 1
+RACE_EXEC_ATOMIC = 2
+RACE_EXEC_ROWS_RED = 3
+
+
+class race_launch(ctypes.Structure):
+    _fields_ = [("executor", ctypes.c_int32), ("group_lanes", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
 
 
 class RaceError(RuntimeError):
@@ -104,6 +115,10 @@ def lib():
     L.race_get_phases.argtypes = [vp, vp, vp, vp]
     L.race_get_info.argtypes = [vp, ctypes.POINTER(race_info)]
     L.race_export.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.race_set_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
+    L.race_get_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
+    L.race_set_launch.restype = ctypes.c_int
+    L.race_get_launch.restype = ctypes.c_int
     L.race_free.argtypes = [vp]
     L.race_free.restype = None
     L.race_strerror.argtypes = [ctypes.c_int]
@@ -232,6 +247,18 @@ def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS,
 
 def symm_spmv(s: Schedule, x, b, stream=None):
     _check(lib().symm_spmv(s.handle, _ptr(x), _ptr(b), _stream(stream)), "symm_spmv")
+
+
+def race_set_launch(s: Schedule, which, executor=0, group_lanes=8, rows_per_group=4, blocks_per_sm=0):
+    """which = 0: symm_spmv, 1: spmv_full."""
+    lc = race_launch(int(executor), int(group_lanes), int(rows_per_group), int(blocks_per_sm))
+    _check(lib().race_set_launch(s.handle, int(which), ctypes.byref(lc)), "race_set_launch")
+
+
+def race_get_launch(s: Schedule, which):
+    lc = race_launch()
+    _check(lib().race_get_launch(s.handle, int(which), ctypes.byref(lc)), "race_get_launch")
+    return {f: getattr(lc, f) for f, _ in lc._fields_}
 
 
 def symm_spmv_exec(s: Schedule, executor, x, b, stream=None):

@@ -200,6 +200,106 @@ __global__ void __launch_bounds__(kBlock) k_spmv_full(int32_t n, const int32_t* 
     }
 }
 
+// Row-block streaming kernels.  A group of G lanes owns U consecutive rows;
+// their nonzeros form one contiguous range that the lanes stream through
+// (coalesced, two independent loads in flight per lane), each lane finding
+// its row by comparing the index against the U+1 row starts.
+template <int U>
+__device__ __forceinline__ int row_of(int32_t idx, const int32_t (&rb)[U + 1]) {
+    int u = 0;
+#pragma unroll
+    for (int j = 1; j < U; ++j) u += (idx >= rb[j]);
+    return u;
+}
+
+// Alg. "SpMV using the CRS format", row-block streaming.
+template <typename VT, int G, int U>
+__global__ void __launch_bounds__(kBlock) k_spmv_rows(int32_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                     const double* __restrict__ x, double* __restrict__ b) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
+    const int64_t nblk = (static_cast<int64_t>(n) + U - 1) / U;
+    for (int64_t blk = gid; blk < nblk; blk += ngroups) {
+        const int32_t r0 = static_cast<int32_t>(blk * U);
+        int32_t rb[U + 1];
+#pragma unroll
+        for (int j = 0; j <= U; ++j) rb[j] = __ldg(rp + min(r0 + j, n));
+        double acc[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) acc[j] = 0.0;
+        int32_t idx = rb[0] + lane;
+        for (; idx + G < rb[U]; idx += 2 * G) {
+            const double a0 = ldv(val + idx), a1 = ldv(val + idx + G);
+            const int32_t c0 = __ldg(col + idx), c1 = __ldg(col + idx + G);
+            const double p0 = a0 * __ldg(x + c0), p1 = a1 * __ldg(x + c1);
+            const int u0 = row_of<U>(idx, rb), u1 = row_of<U>(idx + G, rb);
+#pragma unroll
+            for (int j = 0; j < U; ++j) acc[j] += (u0 == j ? p0 : 0.0) + (u1 == j ? p1 : 0.0);
+        }
+        if (idx < rb[U]) {
+            const double p0 = ldv(val + idx) * __ldg(x + __ldg(col + idx));
+            const int u0 = row_of<U>(idx, rb);
+#pragma unroll
+            for (int j = 0; j < U; ++j) acc[j] += (u0 == j ? p0 : 0.0);
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const double v = group_sum<G>(acc[j], mask);
+            if (lane == j && r0 + j < n) b[r0 + j] = v;
+        }
+    }
+}
+
+// SymmSpMV over all rows at once, row-block streaming; the scatter of the
+// transposed part and the row sums go to b as reductions at L2.
+template <typename VT, int G, int U>
+__global__ void __launch_bounds__(kBlock) k_symm_rows_red(int32_t n, const int32_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                         const double* __restrict__ x, double* b) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
+    const int64_t nblk = (static_cast<int64_t>(n) + U - 1) / U;
+    for (int64_t blk = gid; blk < nblk; blk += ngroups) {
+        const int32_t r0 = static_cast<int32_t>(blk * U);
+        int32_t rb[U + 1];
+        double xr[U];
+#pragma unroll
+        for (int j = 0; j <= U; ++j) rb[j] = __ldg(rp + min(r0 + j, n));
+#pragma unroll
+        for (int j = 0; j < U; ++j) xr[j] = __ldg(x + min(r0 + j, n - 1));
+        double acc[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) acc[j] = 0.0;
+        for (int32_t idx = rb[0] + lane; idx < rb[U]; idx += G) {
+            const double a = ldv(val + idx);
+            const int32_t c = __ldg(col + idx);
+            const int u = row_of<U>(idx, rb);
+            double xrow = xr[0];
+#pragma unroll
+            for (int j = 1; j < U; ++j) xrow = (u == j) ? xr[j] : xrow;
+            double prod;
+            if (c == r0 + u) {
+                prod = a * xrow;  // diagonal
+            } else {
+                prod = a * __ldg(x + c);
+                atomicAdd(b + c, a * xrow);
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j) acc[j] += (u == j ? prod : 0.0);
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const double v = group_sum<G>(acc[j], mask);
+            if (lane == j && r0 + j < n) atomicAdd(b + r0 + j, v);
+        }
+    }
+}
+
 __global__ void k_permute(int32_t n, int32_t k, const int32_t* __restrict__ perm, const double* __restrict__ in,
                           double* __restrict__ out, int inverse) {
     const int64_t total = static_cast<int64_t>(n) * k;
@@ -223,8 +323,9 @@ int sm_count() {
     return g_sm_count;
 }
 
-int grid_for(int64_t threads_needed) {
-    const int64_t cap = static_cast<int64_t>(sm_count()) * (2048 / kBlock);
+int grid_for(int64_t threads_needed, int blocks_per_sm = 0) {
+    const int64_t per_sm = blocks_per_sm > 0 ? blocks_per_sm : (2048 / kBlock);
+    const int64_t cap = static_cast<int64_t>(sm_count()) * per_sm;
     int64_t blocks = (threads_needed + kBlock - 1) / kBlock;
     return static_cast<int>(std::max<int64_t>(1, std::min(blocks, cap)));
 }
@@ -249,6 +350,48 @@ void launch_phases(const race_schedule* s, const double* x, double* b, cudaStrea
             s->d_rp, s->d_col, val, x, b, s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
     }
 }
+
+template <typename VT, int G, int U>
+void launch_rows_red_gu(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const int32_t n = s->plan.n;
+    const int64_t groups = (static_cast<int64_t>(n) + U - 1) / U;
+    k_symm_rows_red<VT, G, U><<<grid_for(groups * G, s->launch.blocks_per_sm), kBlock, 0, st>>>(
+        n, s->d_rp, s->d_col, static_cast<const VT*>(s->d_val), x, b);
+}
+
+template <typename VT, int G, int U>
+void launch_full_gu(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const int32_t n = s->plan.n;
+    const int64_t groups = (static_cast<int64_t>(n) + U - 1) / U;
+    k_spmv_rows<VT, G, U><<<grid_for(groups * G, s->full_launch.blocks_per_sm), kBlock, 0, st>>>(
+        n, s->d_frp, s->d_fcol, static_cast<const VT*>(s->d_fval), x, b);
+}
+
+#define RACE_GU_SWITCH(FN, VT, G, U, ...)                                                 \
+    do {                                                                                  \
+        const int g_ = (G), u_ = (U);                                                     \
+        if (g_ == 4) {                                                                    \
+            if (u_ == 1) FN<VT, 4, 1>(__VA_ARGS__);                                       \
+            else if (u_ == 2) FN<VT, 4, 2>(__VA_ARGS__);                                  \
+            else if (u_ == 4) FN<VT, 4, 4>(__VA_ARGS__);                                  \
+            else FN<VT, 4, 8>(__VA_ARGS__);                                               \
+        } else if (g_ == 8) {                                                             \
+            if (u_ == 1) FN<VT, 8, 1>(__VA_ARGS__);                                       \
+            else if (u_ == 2) FN<VT, 8, 2>(__VA_ARGS__);                                  \
+            else if (u_ == 4) FN<VT, 8, 4>(__VA_ARGS__);                                  \
+            else FN<VT, 8, 8>(__VA_ARGS__);                                               \
+        } else if (g_ == 16) {                                                            \
+            if (u_ == 1) FN<VT, 16, 1>(__VA_ARGS__);                                      \
+            else if (u_ == 2) FN<VT, 16, 2>(__VA_ARGS__);                                 \
+            else if (u_ == 4) FN<VT, 16, 4>(__VA_ARGS__);                                 \
+            else FN<VT, 16, 8>(__VA_ARGS__);                                              \
+        } else {                                                                          \
+            if (u_ == 1) FN<VT, 32, 1>(__VA_ARGS__);                                      \
+            else if (u_ == 2) FN<VT, 32, 2>(__VA_ARGS__);                                 \
+            else if (u_ == 4) FN<VT, 32, 4>(__VA_ARGS__);                                 \
+            else FN<VT, 32, 8>(__VA_ARGS__);                                              \
+        }                                                                                 \
+    } while (0)
 
 template <typename VT, int G>
 void launch_phases_cta(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
@@ -283,6 +426,8 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
         RACE_DISPATCH(launch_phases_cta)
     } else if (exec == RACE_EXEC_ATOMIC) {
         RACE_DISPATCH(launch_atomic)
+    } else if (exec == RACE_EXEC_ROWS_RED) {
+        RACE_GU_SWITCH(launch_rows_red_gu, VT, s->launch.group_lanes, s->launch.rows_per_group, s, x, b, st);
     } else {
         RACE_DISPATCH(launch_phases)
     }
@@ -370,15 +515,15 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
         race_set_detail(std::string("memset: ") + cudaGetErrorString(e));
         return RACE_ERR_CUDA;
     }
-    if (s->val_type == RACE_F64) launch_symm<double>(s, x_d, b_d, st);
-    else launch_symm<float>(s, x_d, b_d, st);
+    if (s->val_type == RACE_F64) launch_symm_exec<double>(s, s->launch.executor, x_d, b_d, st);
+    else launch_symm_exec<float>(s, s->launch.executor, x_d, b_d, st);
     return check_launch("symm_spmv");
 }
 
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_ATOMIC) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_ROWS_RED) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -422,9 +567,41 @@ int spmv_full(const race_schedule* s, const double* x_d, double* b_d, void* stre
         if (rc) return rc;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s->val_type == RACE_F64) launch_full<double>(s, x_d, b_d, st);
-    else launch_full<float>(s, x_d, b_d, st);
+    if (s->val_type == RACE_F64)
+        RACE_GU_SWITCH(launch_full_gu, double, s->full_launch.group_lanes, s->full_launch.rows_per_group, s, x_d, b_d, st);
+    else
+        RACE_GU_SWITCH(launch_full_gu, float, s->full_launch.group_lanes, s->full_launch.rows_per_group, s, x_d, b_d, st);
     return check_launch("spmv_full");
+}
+
+int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
+    if (!s || !l) {
+        race_set_detail("NULL argument");
+        return RACE_ERR_INVALID;
+    }
+    const bool g_ok = l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
+    const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
+    if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_ROWS_RED || (which != 0 && which != 1)) {
+        race_set_detail("launch configuration out of range");
+        return RACE_ERR_INVALID;
+    }
+    if (which == 0) {
+        s->launch = *l;
+        s->group_lanes = l->group_lanes;
+    } else {
+        s->full_launch = *l;
+    }
+    return RACE_OK;
+}
+
+int race_get_launch(const race_schedule* s, int32_t which, race_launch* l) {
+    if (!s || !l || (which != 0 && which != 1)) {
+        race_set_detail("bad argument");
+        return RACE_ERR_INVALID;
+    }
+    *l = which == 0 ? s->launch : s->full_launch;
+    return RACE_OK;
 }
 
 static int permute_impl(const race_schedule* s, const double* in, double* out, int32_t k, void* stream, int inv) {

@@ -182,6 +182,10 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
             std::vector<double>().swap(s->h_val64);
         }
         s->group_lanes = p->group_lanes ? p->group_lanes : pick_lanes(static_cast<int64_t>(s->h_col.size()), a->n);
+        s->launch.executor = RACE_EXEC_LEAF_GROUP;
+        s->launch.group_lanes = s->group_lanes;
+        s->launch.rows_per_group = 4;
+        s->launch.blocks_per_sm = 0;
         s->host_only = (p->flags & RACE_FLAG_HOST_ONLY) ? 1 : 0;
     } catch (const std::bad_alloc&) {
         delete s;
@@ -272,6 +276,12 @@ int race_prepare_full(race_schedule* s, void* stream) {
     s->nnz_full = nnz_full;
     const double per_row = static_cast<double>(nnz_full) / n;
     s->full_lanes = per_row <= 4.5 ? 4 : per_row <= 9.0 ? 8 : per_row <= 18.0 ? 16 : 32;
+    if (s->full_launch.group_lanes == 0) {
+        s->full_launch.executor = 0;
+        s->full_launch.group_lanes = s->full_lanes;
+        s->full_launch.rows_per_group = 4;
+        s->full_launch.blocks_per_sm = 0;
+    }
     return rc;
 }
 

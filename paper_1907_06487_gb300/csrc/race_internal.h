@@ -69,6 +69,8 @@ struct race_schedule {
     int64_t nnz_full = 0;
     int32_t full_lanes = 8;
     int32_t device = 0;
+    race_launch launch{};       // symm_spmv executor and shape
+    race_launch full_launch{};  // spmv_full shape
 };
 
 // Error detail for race_last_error_detail (thread-local).
