@@ -142,9 +142,14 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    sums are reductions at L2 on the permuted
                                    matrix                                   */
 
+#define RACE_EXEC_STREAM_RED 4  /* as ROWS_RED, with row blocks staged into
+                                   shared memory by bulk asynchronous copies
+                                   (multi-stage pipeline, persistent grid)  */
+
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {
-    int32_t executor;        /* RACE_EXEC_* (symm_spmv only)                */
+    int32_t executor;        /* symm_spmv: RACE_EXEC_*; spmv_full: 0 = row
+                                blocks in registers, 1 = staged stream      */
     int32_t group_lanes;     /* lanes per row group: 4, 8, 16 or 32         */
     int32_t rows_per_group;  /* consecutive rows a group streams: 1,2,4,8
                                 (RACE_EXEC_ROWS_RED and spmv_full)          */
@@ -155,6 +160,11 @@ typedef struct {
  * spmv_full.  Out-of-range shapes return RACE_ERR_INVALID.                 */
 int race_set_launch(race_schedule *s, int32_t which, const race_launch *l);
 int race_get_launch(const race_schedule *s, int32_t which, race_launch *l);
+
+/* race_poll_status — synchronises `stream`, then returns RACE_ERR_TIMEOUT
+ * (and clears it) if a bounded device wait of this schedule's kernels gave
+ * up since the last poll, else RACE_OK.                                    */
+int race_poll_status(race_schedule *s, void *stream);
 
 /* symm_spmv_exec — symm_spmv with an explicit executor (RACE_EXEC_*).
  * Same arguments, layout and errors as symm_spmv.                          */

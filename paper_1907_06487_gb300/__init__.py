@@ -41,12 +41,13 @@ PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full",
             "race_prepare_full", "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix",
             "race_get_phases", "race_get_info", "race_export", "race_free", "race_strerror",
-            "race_last_error_detail", "race_set_launch", "race_get_launch")
+            "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
 RACE_EXEC_ATOMIC = 2
 RACE_EXEC_ROWS_RED = 3
+RACE_EXEC_STREAM_RED = 4
 
 
 class race_launch(ctypes.Structure):
@@ -118,6 +119,8 @@ def lib():
     L.race_set_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
     L.race_get_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
     L.race_set_launch.restype = ctypes.c_int
+    L.race_poll_status.argtypes = [vp, vp]
+    L.race_poll_status.restype = ctypes.c_int
     L.race_get_launch.restype = ctypes.c_int
     L.race_free.argtypes = [vp]
     L.race_free.restype = None
@@ -259,6 +262,10 @@ def race_get_launch(s: Schedule, which):
     lc = race_launch()
     _check(lib().race_get_launch(s.handle, int(which), ctypes.byref(lc)), "race_get_launch")
     return {f: getattr(lc, f) for f, _ in lc._fields_}
+
+
+def race_poll_status(s: Schedule, stream=None):
+    _check(lib().race_poll_status(s.handle, _stream(stream)), "race_poll_status")
 
 
 def symm_spmv_exec(s: Schedule, executor, x, b, stream=None):

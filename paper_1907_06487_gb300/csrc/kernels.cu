@@ -426,8 +426,10 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
         RACE_DISPATCH(launch_phases_cta)
     } else if (exec == RACE_EXEC_ATOMIC) {
         RACE_DISPATCH(launch_atomic)
-    } else if (exec == RACE_EXEC_ROWS_RED) {
+    } else if (exec == RACE_EXEC_ROWS_RED || (exec == RACE_EXEC_STREAM_RED && s->max_row_upper > 1024)) {
         RACE_GU_SWITCH(launch_rows_red_gu, VT, s->launch.group_lanes, s->launch.rows_per_group, s, x, b, st);
+    } else if (exec == RACE_EXEC_STREAM_RED) {
+        race_stream_symm_red(s, x, b, st, sm_count());
     } else {
         RACE_DISPATCH(launch_phases)
     }
@@ -523,7 +525,7 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_ROWS_RED) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_STREAM_RED) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -567,7 +569,9 @@ int spmv_full(const race_schedule* s, const double* x_d, double* b_d, void* stre
         if (rc) return rc;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s->val_type == RACE_F64)
+    if (s->full_launch.executor == 1 && s->max_row_full <= 1024)
+        race_stream_full(s, x_d, b_d, st, sm_count());
+    else if (s->val_type == RACE_F64)
         RACE_GU_SWITCH(launch_full_gu, double, s->full_launch.group_lanes, s->full_launch.rows_per_group, s, x_d, b_d, st);
     else
         RACE_GU_SWITCH(launch_full_gu, float, s->full_launch.group_lanes, s->full_launch.rows_per_group, s, x_d, b_d, st);
@@ -582,7 +586,7 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool g_ok = l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
-        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_ROWS_RED || (which != 0 && which != 1)) {
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_STREAM_RED || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
     }
@@ -591,6 +595,29 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
         s->group_lanes = l->group_lanes;
     } else {
         s->full_launch = *l;
+    }
+    return RACE_OK;
+}
+
+int race_poll_status(race_schedule* s, void* stream) {
+    if (!s) {
+        race_set_detail("NULL schedule");
+        return RACE_ERR_INVALID;
+    }
+    if (s->host_only || !s->d_status) return RACE_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("status read: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    if (h != RACE_OK) {
+        cudaMemsetAsync(s->d_status, 0, sizeof(int32_t), st);
+        cudaStreamSynchronize(st);
+        race_set_detail("a bounded device wait gave up");
+        return h;
     }
     return RACE_OK;
 }

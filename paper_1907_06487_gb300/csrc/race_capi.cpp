@@ -26,18 +26,25 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void release_device(race_schedule* s) {
     void* ptrs[] = {s->d_rp, s->d_col, s->d_val, s->d_leaf_lo, s->d_leaf_hi, s->d_perm,
-                    s->d_frp, s->d_fcol, s->d_fval};
+                    s->d_frp, s->d_fcol, s->d_fval, s->d_blk, s->d_fblk, s->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
+    s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
 }
 
+// Streamed arrays get kStreamPad zeroed elements after their end so that
+// copies widened to 16-byte multiples stay inside the allocation.
+constexpr size_t kStreamPad = 8;
+
 template <typename T>
-int upload(const std::vector<T>& h, T** d, cudaStream_t st) {
-    const size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+int upload(const std::vector<T>& h, T** d, cudaStream_t st, size_t pad = kStreamPad) {
+    const size_t bytes = (h.size() + pad) * sizeof(T);
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d), bytes);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(RACE_ERR_NOMEM, "cudaMalloc") : cuda_fail(e, "cudaMalloc");
+    e = cudaMemsetAsync(*d, 0, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (!h.empty()) {
         e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
@@ -131,6 +138,24 @@ int pick_lanes(int64_t nnz, int32_t n) {
 
 void race_set_detail(const std::string& s) { g_detail = s; }
 
+std::vector<int32_t> race_row_blocks(const int32_t* rp, int32_t n, int32_t max_nnz, int32_t max_rows) {
+    std::vector<int32_t> out(1, 0);
+    int32_t r0 = 0;
+    while (r0 < n) {
+        int32_t r = r0 + 1;
+        while (r < n && r - r0 < max_rows && rp[r + 1] - rp[r0] <= max_nnz) ++r;
+        out.push_back(r);
+        r0 = r;
+    }
+    return out;
+}
+
+int32_t race_max_row(const int32_t* rp, int32_t n) {
+    int32_t m = 0;
+    for (int32_t r = 0; r < n; ++r) m = std::max(m, rp[r + 1] - rp[r]);
+    return m;
+}
+
 extern "C" {
 
 void race_default_params(race_params* p, int32_t n_workers) {
@@ -211,6 +236,16 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
             s->d_val = d;
         }
         if (rc == RACE_OK) {
+            std::vector<int32_t> blk = race_row_blocks(s->h_rp.data(), a->n, 1024, 256);
+            s->n_blk = static_cast<int64_t>(blk.size()) - 1;
+            s->max_row_upper = race_max_row(s->h_rp.data(), a->n);
+            rc = upload(blk, &s->d_blk, st);
+        }
+        if (rc == RACE_OK) {
+            std::vector<int32_t> z(1, 0);
+            rc = upload(z, &s->d_status, st);
+        }
+        if (rc == RACE_OK) {
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) rc = cuda_fail(e, "upload");
         }
@@ -270,6 +305,12 @@ int race_prepare_full(race_schedule* s, void* stream) {
         }
     }
     if (rc == RACE_OK) {
+        std::vector<int32_t> blk = race_row_blocks(frp.data(), n, 1024, 256);
+        s->n_fblk = static_cast<int64_t>(blk.size()) - 1;
+        s->max_row_full = race_max_row(frp.data(), n);
+        rc = upload(blk, &s->d_fblk, st);
+    }
+    if (rc == RACE_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "full upload");
     }
@@ -277,7 +318,7 @@ int race_prepare_full(race_schedule* s, void* stream) {
     const double per_row = static_cast<double>(nnz_full) / n;
     s->full_lanes = per_row <= 4.5 ? 4 : per_row <= 9.0 ? 8 : per_row <= 18.0 ? 16 : 32;
     if (s->full_launch.group_lanes == 0) {
-        s->full_launch.executor = 0;
+        s->full_launch.executor = 1;
         s->full_launch.group_lanes = s->full_lanes;
         s->full_launch.rows_per_group = 4;
         s->full_launch.blocks_per_sm = 0;

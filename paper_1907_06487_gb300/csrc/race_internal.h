@@ -4,6 +4,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/race.h"
 
 namespace race {
@@ -69,9 +71,24 @@ struct race_schedule {
     int64_t nnz_full = 0;
     int32_t full_lanes = 8;
     int32_t device = 0;
+    int32_t* d_blk = nullptr;   // row-block starts of the upper CRS (streaming)
+    int64_t n_blk = 0;
+    int32_t* d_fblk = nullptr;  // row-block starts of the full CRS
+    int64_t n_fblk = 0;
+    int32_t* d_status = nullptr;  // device status word (RACE_ERR_TIMEOUT)
+    int32_t max_row_upper = 0, max_row_full = 0;
     race_launch launch{};       // symm_spmv executor and shape
     race_launch full_launch{};  // spmv_full shape
 };
+
+// Row blocks for the streaming kernels: consecutive rows with at most
+// max_nnz nonzeros and max_rows rows each (a longer row gets a block alone).
+std::vector<int32_t> race_row_blocks(const int32_t* rp, int32_t n, int32_t max_nnz, int32_t max_rows);
+int32_t race_max_row(const int32_t* rp, int32_t n);
+
+// Streaming launchers (stream_kernels.cu).
+int race_stream_full(const race_schedule* s, const double* x, double* b, cudaStream_t st, int sm_count);
+int race_stream_symm_red(const race_schedule* s, const double* x, double* b, cudaStream_t st, int sm_count);
 
 // Error detail for race_last_error_detail (thread-local).
 void race_set_detail(const std::string& s);
