@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""SymmSpMV benchmark on GB300 (one JSON line on stdout).
+
+Workload (default): the periodic Heisenberg XXZ chain L=26, Sz=0 sector
+(10,400,600 rows, 80,708,656 stored upper nonzeros, 151,016,712 full
+nonzeros), FP64 values, x ~ U[-1,1) (seed 3) -- a synthetic stand-in for the
+paper's Spin-26 matrix.  One step = one b = A x through the library's
+SymmSpMV path (schedule built before timing, as the paper excludes
+preprocessing).  The full-CRS SpMV of the same permuted matrix is timed
+beside it as the traffic baseline.
+
+Timing: W warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), CUDA events on the stream the kernels run on;
+vectors rotate through ring buffers of 4 x and 4 b (each 83 MB) and the
+matrix is 1.05 GB, so every step's inputs exceed the 129 MB L2.  Several
+GPUs (torchrun) run independent replicas (no data exchange); value is the
+sum over ranks of the flops divided by the slowest rank's time.
+
+--impl reference times the CPU oracle (serial FP64 Alg. "SymmSpMV") on a
+bounded number of sweeps of the same matrix on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_DESC = {
+    "xxz26": "Heisenberg XXZ chain L=26 periodic, Sz=0 (10,400,600 rows), J=1, Delta=1, FP64 upper CRS, "
+             "x~U[-1,1) seed 3, RACE-permuted",
+    "st27_200": "3D 27-point stencil 200^3 nonperiodic SPD, off-diag -U(0,1] seed 4, FP64 upper CRS",
+    "anderson32": "3D Anderson 32^3 periodic 7-pt, disorder U[-8.25,8.25) seed 1, FP64 upper CRS",
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1907_06487_gb300", "csrc")
+    for name in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on these sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("sources") != kernel_sources_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sweeps(m, seconds):
+    """Serial FP64 Alg. SymmSpMV of the oracle, repeated for about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_1907_06487_gb300 import configs
+    x = configs.vectors("xxz26", m["n"]) if m["n"] == 10400600 else np.ones(m["n"])
+    oracle.symm_spmv(m, x)  # warm
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        oracle.symm_spmv(m, x)
+        k += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return k, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1907_06487_gb300 import configs, perfmodel as pm
+    m = configs.matrix(args.workload)
+    n, nu = m["n"], len(m["col"])
+    nf = 2 * nu - n
+    per_step = max(1.0, args.ref_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sweeps(m, 0.0)
+    k, dt = oracle_sweeps(m, per_step * args.steps)
+    gflops = pm.flops(nf) * k / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "SymmSpMV GFLOP/s", "value": gflops, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / k * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, args.workload)},
+        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{k} full serial SymmSpMV sweeps of the {args.workload} matrix"},
+        "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1907_06487_gb300 as R
+    from paper_1907_06487_gb300 import build as B, configs, perfmodel as pm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    R.lib()
+
+    name = args.workload
+    m = configs.matrix(name)
+    cfg = configs.SCHEDULE[name]
+    n, nu = m["n"], len(m["col"])
+    nf = 2 * nu - n
+    t0 = time.perf_counter()
+    stream = torch.cuda.Stream(device=dev)
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream)
+    build_s = time.perf_counter() - t0
+    lc = cfg["launch"]
+    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"])
+    fl = cfg["full_launch"]
+    R.race_prepare_full(s, stream)
+    R.race_set_launch(s, 1, fl["executor"], fl["group_lanes"], fl["rows_per_group"], fl["blocks_per_sm"])
+    info = s.info()
+    perm = s.perm()
+    x_host = configs.vectors(name, n)
+
+    ring = 4
+    with torch.cuda.stream(stream):
+        xs = []
+        for i in range(ring):
+            xo = torch.from_numpy(x_host).to(dev) if i == 0 else torch.rand(n, dtype=torch.float64, device=dev)
+            xp = torch.empty_like(xo)
+            R.race_permute(s, xo, xp, 1, stream)
+            xs.append(xp)
+        bs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(ring)]
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(fn, steps, warmup):
+        for i in range(warmup):
+            fn(i)
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            fn(i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return e0.elapsed_time(e1) * 1e-3
+
+    # ---- main timed region: SymmSpMV -------------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t_symm = timed(lambda i: R.symm_spmv(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    clk = clocks.stop()
+    R.race_poll_status(s, stream)
+    # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
+    t_full = timed(lambda i: R.spmv_full(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    # ---- end to end through host buffers: H2D x, permute, SymmSpMV, unpermute, D2H b --------
+    xh = torch.from_numpy(x_host).pin_memory()
+    bh = torch.empty(n, dtype=torch.float64).pin_memory()
+    xd, xpd, bpd, bd = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(4))
+
+    def e2e_step(_):
+        xd.copy_(xh, non_blocking=True)
+        R.race_permute(s, xd, xpd, 1, stream)
+        R.symm_spmv(s, xpd, bpd, stream)
+        R.race_unpermute(s, bpd, bd, 1, stream)
+        bh.copy_(bd, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        t_e2e = timed(e2e_step, args.steps, args.warmup)
+    # max over ranks
+    times = torch.tensor([t_symm, t_full, t_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    t_symm, t_full, t_e2e = (float(v) for v in times.cpu())
+
+    flops = pm.flops(nf)
+    per_step = t_symm / args.steps
+    value = world * flops * args.steps / t_symm / 1e9
+    full_gflops = world * flops * args.steps / t_full / 1e9
+    e2e_value = world * flops * args.steps / t_e2e / 1e9
+    sym_bytes = pm.symm_bytes(n, nu)
+    achieved = sym_bytes / per_step / 1e9
+    peak, peak_kind = load_peaks()
+    launches_per_step = 1 if lc["executor"] >= R.RACE_EXEC_ATOMIC else info["n_phases"]
+    if rank != 0:
+        return 0
+
+    # CPU baseline: the oracle on a bounded sample (a few serial sweeps)
+    cpu = None
+    if not args.no_cpu_baseline:
+        k, dt = oracle_sweeps(m, args.cpu_seconds)
+        cpu = {"value": flops * k / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} full serial SymmSpMV sweeps (oracle, FP64) of the {name} matrix, {dt:.1f} s"}
+    traffic = ncu_traffic(name, "symm")
+    line = {
+        "metric": "SymmSpMV GFLOP/s (2*nnz_full flops per step) on 1 GB300 vs full-CRS SpMV",
+        "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "desc": WORKLOAD_DESC.get(name, name), "n": n, "nnz_upper": nu, "nnz_full": nf,
+                   "l2": "inputs larger than L2 (matrix 1.05 GB; x, b rotate over 4+4 buffers of 83 MB)",
+                   "schedule": {"n_workers": cfg["n_workers"], "eps": list(cfg["eps"]), "n_phases": info["n_phases"],
+                                "eta": info["eta"], "depth": info["depth"]},
+                   "launch": lc, "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_step": sym_bytes},
+        "symm_gbs": achieved,
+        "spmv_full": {"value": full_gflops, "unit": "GFLOP/s", "ms_per_step": t_full / args.steps * 1e3,
+                      "gbs": pm.full_bytes(n, nf) / (t_full / args.steps) / 1e9},
+        "speedup_vs_full": t_full / t_symm,
+        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "build_seconds": build_s,
+    }
+    print(json.dumps(line))
+    s.free()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="xxz26", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

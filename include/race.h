@@ -150,7 +150,7 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
 typedef struct {
     int32_t executor;        /* symm_spmv: RACE_EXEC_*; spmv_full: 0 = row
                                 blocks in registers, 1 = staged stream      */
-    int32_t group_lanes;     /* lanes per row group: 4, 8, 16 or 32         */
+    int32_t group_lanes;     /* lanes per row group: 1, 2, 4, 8, 16 or 32   */
     int32_t rows_per_group;  /* consecutive rows a group streams: 1,2,4,8
                                 (RACE_EXEC_ROWS_RED and spmv_full)          */
     int32_t blocks_per_sm;   /* resident 256-thread blocks per SM, 0 = max  */

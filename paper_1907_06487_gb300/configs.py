@@ -22,11 +22,14 @@ from . import matgen
 
 SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 
-# schedule parameters per workload: n_workers, eps, max_depth, executor
+# schedule parameters per workload: n_workers, eps, max_depth, the executor
+# tested at full size, and the launch shapes of symm_spmv / spmv_full
+_L = dict(executor=3, group_lanes=4, rows_per_group=1, blocks_per_sm=0)
+_F = dict(executor=0, group_lanes=4, rows_per_group=1, blocks_per_sm=0)
 SCHEDULE = {
-    "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1),
-    "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1),
-    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1),
+    "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
+    "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
+    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
 }
 
 

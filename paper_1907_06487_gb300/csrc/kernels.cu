@@ -230,20 +230,25 @@ __global__ void __launch_bounds__(kBlock) k_spmv_rows(int32_t n, const int32_t* 
         double acc[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) acc[j] = 0.0;
-        int32_t idx = rb[0] + lane;
-        for (; idx + G < rb[U]; idx += 2 * G) {
-            const double a0 = ldv(val + idx), a1 = ldv(val + idx + G);
-            const int32_t c0 = __ldg(col + idx), c1 = __ldg(col + idx + G);
-            const double p0 = a0 * __ldg(x + c0), p1 = a1 * __ldg(x + c1);
-            const int u0 = row_of<U>(idx, rb), u1 = row_of<U>(idx + G, rb);
+        // four independent entries per lane and iteration
+        for (int32_t idx = rb[0] + lane; idx < rb[U]; idx += 4 * G) {
+            double a[4], p[4];
+            int32_t c[4];
 #pragma unroll
-            for (int j = 0; j < U; ++j) acc[j] += (u0 == j ? p0 : 0.0) + (u1 == j ? p1 : 0.0);
-        }
-        if (idx < rb[U]) {
-            const double p0 = ldv(val + idx) * __ldg(x + __ldg(col + idx));
-            const int u0 = row_of<U>(idx, rb);
+            for (int t = 0; t < 4; ++t) {
+                const int32_t j = idx + t * G;
+                const bool v = j < rb[U];
+                a[t] = v ? ldv(val + j) : 0.0;
+                c[t] = v ? __ldg(col + j) : -1;
+            }
 #pragma unroll
-            for (int j = 0; j < U; ++j) acc[j] += (u0 == j ? p0 : 0.0);
+            for (int t = 0; t < 4; ++t) p[t] = c[t] >= 0 ? a[t] * __ldg(x + c[t]) : 0.0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int u = row_of<U>(idx + t * G, rb);
+#pragma unroll
+                for (int j = 0; j < U; ++j) acc[j] += (u == j ? p[t] : 0.0);
+            }
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) {
@@ -275,22 +280,31 @@ __global__ void __launch_bounds__(kBlock) k_symm_rows_red(int32_t n, const int32
         double acc[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) acc[j] = 0.0;
-        for (int32_t idx = rb[0] + lane; idx < rb[U]; idx += G) {
-            const double a = ldv(val + idx);
-            const int32_t c = __ldg(col + idx);
-            const int u = row_of<U>(idx, rb);
-            double xrow = xr[0];
+        // four independent entries per lane and iteration
+        for (int32_t idx = rb[0] + lane; idx < rb[U]; idx += 4 * G) {
+            double a[4], xc[4];
+            int32_t c[4];
 #pragma unroll
-            for (int j = 1; j < U; ++j) xrow = (u == j) ? xr[j] : xrow;
-            double prod;
-            if (c == r0 + u) {
-                prod = a * xrow;  // diagonal
-            } else {
-                prod = a * __ldg(x + c);
-                atomicAdd(b + c, a * xrow);
+            for (int t = 0; t < 4; ++t) {
+                const int32_t j = idx + t * G;
+                const bool v = j < rb[U];
+                a[t] = v ? ldv(val + j) : 0.0;
+                c[t] = v ? __ldg(col + j) : -1;
             }
 #pragma unroll
-            for (int j = 0; j < U; ++j) acc[j] += (u == j ? prod : 0.0);
+            for (int t = 0; t < 4; ++t) xc[t] = c[t] >= 0 ? __ldg(x + c[t]) : 0.0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (c[t] < 0) continue;
+                const int u = row_of<U>(idx + t * G, rb);
+                double xrow = xr[0];
+#pragma unroll
+                for (int j = 1; j < U; ++j) xrow = (u == j) ? xr[j] : xrow;
+                const double prod = a[t] * xc[t];
+                if (c[t] != r0 + u) atomicAdd(b + c[t], a[t] * xrow);  // transposed part
+#pragma unroll
+                for (int j = 0; j < U; ++j) acc[j] += (u == j ? prod : 0.0);
+            }
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) {
@@ -367,30 +381,22 @@ void launch_full_gu(const race_schedule* s, const double* x, double* b, cudaStre
         n, s->d_frp, s->d_fcol, static_cast<const VT*>(s->d_fval), x, b);
 }
 
-#define RACE_GU_SWITCH(FN, VT, G, U, ...)                                                 \
-    do {                                                                                  \
-        const int g_ = (G), u_ = (U);                                                     \
-        if (g_ == 4) {                                                                    \
-            if (u_ == 1) FN<VT, 4, 1>(__VA_ARGS__);                                       \
-            else if (u_ == 2) FN<VT, 4, 2>(__VA_ARGS__);                                  \
-            else if (u_ == 4) FN<VT, 4, 4>(__VA_ARGS__);                                  \
-            else FN<VT, 4, 8>(__VA_ARGS__);                                               \
-        } else if (g_ == 8) {                                                             \
-            if (u_ == 1) FN<VT, 8, 1>(__VA_ARGS__);                                       \
-            else if (u_ == 2) FN<VT, 8, 2>(__VA_ARGS__);                                  \
-            else if (u_ == 4) FN<VT, 8, 4>(__VA_ARGS__);                                  \
-            else FN<VT, 8, 8>(__VA_ARGS__);                                               \
-        } else if (g_ == 16) {                                                            \
-            if (u_ == 1) FN<VT, 16, 1>(__VA_ARGS__);                                      \
-            else if (u_ == 2) FN<VT, 16, 2>(__VA_ARGS__);                                 \
-            else if (u_ == 4) FN<VT, 16, 4>(__VA_ARGS__);                                 \
-            else FN<VT, 16, 8>(__VA_ARGS__);                                              \
-        } else {                                                                          \
-            if (u_ == 1) FN<VT, 32, 1>(__VA_ARGS__);                                      \
-            else if (u_ == 2) FN<VT, 32, 2>(__VA_ARGS__);                                 \
-            else if (u_ == 4) FN<VT, 32, 4>(__VA_ARGS__);                                 \
-            else FN<VT, 32, 8>(__VA_ARGS__);                                              \
-        }                                                                                 \
+#define RACE_U_SWITCH(FN, VT, GG, u_, ...)          \
+    do {                                            \
+        if ((u_) == 1) FN<VT, GG, 1>(__VA_ARGS__);   \
+        else if ((u_) == 2) FN<VT, GG, 2>(__VA_ARGS__); \
+        else if ((u_) == 4) FN<VT, GG, 4>(__VA_ARGS__); \
+        else FN<VT, GG, 8>(__VA_ARGS__);             \
+    } while (0)
+#define RACE_GU_SWITCH(FN, VT, G, U, ...)                                  \
+    do {                                                                   \
+        const int g_ = (G), u_ = (U);                                      \
+        if (g_ == 1) RACE_U_SWITCH(FN, VT, 1, u_, __VA_ARGS__);            \
+        else if (g_ == 2) RACE_U_SWITCH(FN, VT, 2, u_, __VA_ARGS__);       \
+        else if (g_ == 4) RACE_U_SWITCH(FN, VT, 4, u_, __VA_ARGS__);       \
+        else if (g_ == 8) RACE_U_SWITCH(FN, VT, 8, u_, __VA_ARGS__);       \
+        else if (g_ == 16) RACE_U_SWITCH(FN, VT, 16, u_, __VA_ARGS__);     \
+        else RACE_U_SWITCH(FN, VT, 32, u_, __VA_ARGS__);                   \
     } while (0)
 
 template <typename VT, int G>
@@ -583,7 +589,7 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
         race_set_detail("NULL argument");
         return RACE_ERR_INVALID;
     }
-    const bool g_ok = l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
+    const bool g_ok = l->group_lanes == 1 || l->group_lanes == 2 || l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
         l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_STREAM_RED || (which != 0 && which != 1)) {
