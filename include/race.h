@@ -146,14 +146,23 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    shared memory by bulk asynchronous copies
                                    (multi-stage pipeline, persistent grid)  */
 
+#define RACE_EXEC_PIPE_RED   5  /* one row per thread, software-pipelined over
+                                   the thread's rows (x gathers of row i,
+                                   val/col of row i+1 and row pointers of row
+                                   i+2 in flight together); updates of b as
+                                   reductions at L2                         */
+
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {
     int32_t executor;        /* symm_spmv: RACE_EXEC_*; spmv_full: 0 = row
-                                blocks in registers, 1 = staged stream      */
+                                blocks in registers, 1 = staged stream,
+                                2 = one row per thread, pipelined           */
     int32_t group_lanes;     /* lanes per row group: 1, 2, 4, 8, 16 or 32   */
     int32_t rows_per_group;  /* consecutive rows a group streams: 1,2,4,8
                                 (RACE_EXEC_ROWS_RED and spmv_full)          */
     int32_t blocks_per_sm;   /* resident 256-thread blocks per SM, 0 = max  */
+    int32_t regs_per_row;    /* row entries held in registers by the
+                                pipelined executors: 4, 8 or 16             */
 } race_launch;
 
 /* race_set_launch / race_get_launch — which = 0: symm_spmv, which = 1:

@@ -48,11 +48,12 @@ RACE_EXEC_LEAF_CTA = 1
 RACE_EXEC_ATOMIC = 2
 RACE_EXEC_ROWS_RED = 3
 RACE_EXEC_STREAM_RED = 4
+RACE_EXEC_PIPE_RED = 5
 
 
 class race_launch(ctypes.Structure):
     _fields_ = [("executor", ctypes.c_int32), ("group_lanes", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("regs_per_row", ctypes.c_int32)]
 
 
 class RaceError(RuntimeError):
@@ -252,9 +253,10 @@ def symm_spmv(s: Schedule, x, b, stream=None):
     _check(lib().symm_spmv(s.handle, _ptr(x), _ptr(b), _stream(stream)), "symm_spmv")
 
 
-def race_set_launch(s: Schedule, which, executor=0, group_lanes=8, rows_per_group=4, blocks_per_sm=0):
+def race_set_launch(s: Schedule, which, executor=0, group_lanes=8, rows_per_group=4, blocks_per_sm=0,
+                    regs_per_row=8):
     """which = 0: symm_spmv, 1: spmv_full."""
-    lc = race_launch(int(executor), int(group_lanes), int(rows_per_group), int(blocks_per_sm))
+    lc = race_launch(int(executor), int(group_lanes), int(rows_per_group), int(blocks_per_sm), int(regs_per_row))
     _check(lib().race_set_launch(s.handle, int(which), ctypes.byref(lc)), "race_set_launch")
 
 

@@ -314,6 +314,91 @@ __global__ void __launch_bounds__(kBlock) k_symm_rows_red(int32_t n, const int32
     }
 }
 
+// One row per thread, software-pipelined over the thread's rows (rows
+// tid, tid + T, tid + 2T, ... with T threads in the grid, so a warp holds 32
+// consecutive rows at each step).  Each iteration has three independent load
+// groups in flight: the x gathers of row i, the val/col of row i+1 and the
+// row pointers of row i+2.  The first P entries of a row live in registers;
+// longer rows finish their tail with plain loads.
+//   SYMM = false: b[r] = sum (full CRS, Alg. "SpMV using the CRS format").
+//   SYMM = true : upper CRS; the transposed updates and the row sums are
+//                 reductions at L2 into b (zeroed before).
+template <typename VT, int P, bool SYMM>
+__global__ void __launch_bounds__(kBlock) k_rows_pipe(int32_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                     const double* __restrict__ x, double* b) {
+    const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
+    int64_t r0 = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+    if (r0 >= n) return;
+    int64_t r1 = r0 + T;
+    int32_t rs0 = __ldg(rp + r0), re0 = __ldg(rp + r0 + 1);
+    int32_t rs1 = 0, re1 = 0;
+    if (r1 < n) {
+        rs1 = __ldg(rp + r1);
+        re1 = __ldg(rp + r1 + 1);
+    }
+    double a0[P];
+    int32_t c0[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const bool v = rs0 + p < re0;
+        a0[p] = v ? ldv(val + rs0 + p) : 0.0;
+        c0[p] = v ? __ldg(col + rs0 + p) : -1;
+    }
+    while (true) {
+        // x gathers of the current row
+        double x0[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) x0[p] = c0[p] >= 0 ? __ldg(x + c0[p]) : 0.0;
+        const double xr = SYMM ? __ldg(x + r0) : 0.0;
+        // val/col of the next row
+        double a1[P];
+        int32_t c1[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const bool v = rs1 + p < re1;
+            a1[p] = v ? ldv(val + rs1 + p) : 0.0;
+            c1[p] = v ? __ldg(col + rs1 + p) : -1;
+        }
+        // row pointers of the row after next
+        const int64_t r2 = r1 + T;
+        int32_t rs2 = 0, re2 = 0;
+        if (r2 < n) {
+            rs2 = __ldg(rp + r2);
+            re2 = __ldg(rp + r2 + 1);
+        }
+        // current row
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (c0[p] < 0) continue;
+            acc += a0[p] * x0[p];
+            if (SYMM && c0[p] != r0) atomicAdd(b + c0[p], a0[p] * xr);
+        }
+        for (int32_t j = rs0 + P; j < re0; ++j) {
+            const double a = ldv(val + j);
+            const int32_t c = __ldg(col + j);
+            acc += a * __ldg(x + c);
+            if (SYMM && c != r0) atomicAdd(b + c, a * xr);
+        }
+        if (SYMM) atomicAdd(b + r0, acc);
+        else b[r0] = acc;
+        // rotate the pipeline
+        if (r1 >= n) break;
+        r0 = r1;
+        rs0 = rs1;
+        re0 = re1;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            a0[p] = a1[p];
+            c0[p] = c1[p];
+        }
+        r1 = r2;
+        rs1 = rs2;
+        re1 = re2;
+    }
+}
+
 __global__ void k_permute(int32_t n, int32_t k, const int32_t* __restrict__ perm, const double* __restrict__ in,
                           double* __restrict__ out, int inverse) {
     const int64_t total = static_cast<int64_t>(n) * k;
@@ -381,6 +466,16 @@ void launch_full_gu(const race_schedule* s, const double* x, double* b, cudaStre
         n, s->d_frp, s->d_fcol, static_cast<const VT*>(s->d_fval), x, b);
 }
 
+template <typename VT, bool SYMM>
+void launch_pipe(int32_t n, const int32_t* rp, const int32_t* col, const void* val, const double* x, double* b,
+                 const race_launch& l, cudaStream_t st) {
+    const int g = grid_for(n, l.blocks_per_sm);
+    const VT* v = static_cast<const VT*>(val);
+    if (l.regs_per_row <= 4) k_rows_pipe<VT, 4, SYMM><<<g, kBlock, 0, st>>>(n, rp, col, v, x, b);
+    else if (l.regs_per_row <= 8) k_rows_pipe<VT, 8, SYMM><<<g, kBlock, 0, st>>>(n, rp, col, v, x, b);
+    else k_rows_pipe<VT, 16, SYMM><<<g, kBlock, 0, st>>>(n, rp, col, v, x, b);
+}
+
 #define RACE_U_SWITCH(FN, VT, GG, u_, ...)          \
     do {                                            \
         if ((u_) == 1) FN<VT, GG, 1>(__VA_ARGS__);   \
@@ -436,6 +531,8 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
         RACE_GU_SWITCH(launch_rows_red_gu, VT, s->launch.group_lanes, s->launch.rows_per_group, s, x, b, st);
     } else if (exec == RACE_EXEC_STREAM_RED) {
         race_stream_symm_red(s, x, b, st, sm_count());
+    } else if (exec == RACE_EXEC_PIPE_RED) {
+        launch_pipe<VT, true>(s->plan.n, s->d_rp, s->d_col, s->d_val, x, b, s->launch, st);
     } else {
         RACE_DISPATCH(launch_phases)
     }
@@ -531,7 +628,7 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_STREAM_RED) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_PIPE_RED) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -577,6 +674,10 @@ int spmv_full(const race_schedule* s, const double* x_d, double* b_d, void* stre
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->full_launch.executor == 1 && s->max_row_full <= 1024)
         race_stream_full(s, x_d, b_d, st, sm_count());
+    else if (s->full_launch.executor == 2 && s->val_type == RACE_F64)
+        launch_pipe<double, false>(s->plan.n, s->d_frp, s->d_fcol, s->d_fval, x_d, b_d, s->full_launch, st);
+    else if (s->full_launch.executor == 2)
+        launch_pipe<float, false>(s->plan.n, s->d_frp, s->d_fcol, s->d_fval, x_d, b_d, s->full_launch, st);
     else if (s->val_type == RACE_F64)
         RACE_GU_SWITCH(launch_full_gu, double, s->full_launch.group_lanes, s->full_launch.rows_per_group, s, x_d, b_d, st);
     else
@@ -592,7 +693,7 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool g_ok = l->group_lanes == 1 || l->group_lanes == 2 || l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
-        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_STREAM_RED || (which != 0 && which != 1)) {
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_PIPE_RED || l->regs_per_row < 0 || l->regs_per_row > 16 || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
     }

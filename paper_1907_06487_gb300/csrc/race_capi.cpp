@@ -211,6 +211,7 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
         s->launch.group_lanes = s->group_lanes;
         s->launch.rows_per_group = 4;
         s->launch.blocks_per_sm = 0;
+        s->launch.regs_per_row = 8;
         s->host_only = (p->flags & RACE_FLAG_HOST_ONLY) ? 1 : 0;
     } catch (const std::bad_alloc&) {
         delete s;
@@ -322,6 +323,7 @@ int race_prepare_full(race_schedule* s, void* stream) {
         s->full_launch.group_lanes = s->full_lanes;
         s->full_launch.rows_per_group = 4;
         s->full_launch.blocks_per_sm = 0;
+        s->full_launch.regs_per_row = 16;
     }
     return rc;
 }
