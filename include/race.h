@@ -222,6 +222,38 @@ int race_get_info(const race_schedule *s, race_info *info);
  * n_sublevels, n_children, phase_count, phase_offset; int64 size, neff.    */
 int race_export(const race_schedule *s, void *buf, size_t *size);
 
+/* symm_spmv_noalloc — b = A x like symm_spmv, for callers that must not
+ * allocate device memory themselves or through this library: for example a
+ * plug-in whose host application owns every device allocation, code that
+ * runs under a fixed device-memory budget, or a latency-critical loop where
+ * cudaMalloc's implicit device synchronisation is not acceptable.  The paper
+ * has no counterpart; it is a variant of the streaming SymmSpMV kernel
+ * (RACE_EXEC_STREAM_RED) that needs no schedule handle.
+ *
+ * Arguments (all device pointers owned by the caller): an upper-triangle
+ * CRS with n rows and nnz stored entries -- row_ptr_d (n+1, row_ptr[0] = 0),
+ * col_d and val_d (nnz, FP64), each row's columns >= the row index; any
+ * row order the caller chooses (e.g. a schedule's permuted matrix);
+ * x_d (n) and b_d (n), not aliasing.  b is overwritten.
+ *
+ * Scratch: the kernel's row-block table and status word live in a fixed
+ * device array of about 3.4 MB that every GPU loading the library holds
+ * until the process exits; nothing is allocated per call.  Limits: n at most
+ * 16,777,216 and nnz at most 268,435,456 (RACE_ERR_OVERFLOW beyond), no row
+ * with more than 512 stored entries (RACE_ERR_UNSUPPORTED).
+ *
+ * The first call on a device looks up the device address of that array (a
+ * one-time set-up per device, with that device current); make that first
+ * call before any stream capture.  Every call shares the one array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams or threads) race with each other: serialise them.  The call
+ * enqueues its work on `stream` and waits for that stream twice (to size the
+ * launch and to read the status), so it returns only when b is complete.
+ * Errors: RACE_ERR_INVALID, _OVERFLOW, _UNSUPPORTED, _CUDA, _TIMEOUT; on an
+ * error b is undefined.                                                    */
+int symm_spmv_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr_d, const int32_t *col_d, const double *val_d,
+                      const double *x_d, double *b_d, void *stream);
+
 void race_free(race_schedule *s);
 const char *race_strerror(int code);
 const char *race_last_error_detail(void);

@@ -41,7 +41,8 @@ PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full",
             "race_prepare_full", "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix",
             "race_get_phases", "race_get_info", "race_export", "race_free", "race_strerror",
-            "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status")
+            "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status",
+            "symm_spmv_noalloc")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -122,6 +123,8 @@ def lib():
     L.race_set_launch.restype = ctypes.c_int
     L.race_poll_status.argtypes = [vp, vp]
     L.race_poll_status.restype = ctypes.c_int
+    L.symm_spmv_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, vp, vp, vp, vp]
+    L.symm_spmv_noalloc.restype = ctypes.c_int
     L.race_get_launch.restype = ctypes.c_int
     L.race_free.argtypes = [vp]
     L.race_free.restype = None
@@ -268,6 +271,12 @@ def race_get_launch(s: Schedule, which):
 
 def race_poll_status(s: Schedule, stream=None):
     _check(lib().race_poll_status(s.handle, _stream(stream)), "race_poll_status")
+
+
+def symm_spmv_noalloc(n, nnz, row_ptr, col, val, x, b, stream=None):
+    """The non-allocating SymmSpMV: every argument is a caller-owned device array."""
+    _check(lib().symm_spmv_noalloc(int(n), int(nnz), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(b),
+                                   _stream(stream)), "symm_spmv_noalloc")
 
 
 def symm_spmv_exec(s: Schedule, executor, x, b, stream=None):

@@ -13,7 +13,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
+#include <mutex>
+#include <string>
 
 #include "race_internal.h"
 #include "stream_engine.cuh"
@@ -171,4 +174,234 @@ int race_stream_symm_red(const race_schedule* s, const double* x, double* b, cud
     return race_dev::launch_stream<float, race_dev::kSymmRed>(s->n_blk, s->d_blk, s->d_rp, s->d_col,
                                                               static_cast<const float*>(s->d_val), x, b, s->d_status,
                                                               sm_count, s->launch.blocks_per_sm, st);
+}
+
+// ===========================================================================
+// symm_spmv_noalloc: the streaming SymmSpMV for callers that may not
+// allocate device memory.
+//
+// The streaming kernel above needs scratch memory besides its inputs and
+// outputs: a table of row-block starts and a status word.  A schedule keeps
+// them in memory that race_build allocates; this variant keeps them in one
+// file-scope device array instead, fixed at load time, so the call itself
+// allocates nothing.  The block table is rebuilt on the device at every call
+// from the caller's row pointers (a block ends every 64 rows and whenever
+// the next row starts in a new 512-entry chunk of the nonzeros, so a block
+// holds at most 64 rows and 1023 nonzeros when no row is longer than 512).
+// Blocks whose 16-byte-widened copies would read past the caller's arrays
+// (the last one or two) are handled by a plain-load tail kernel instead.
+// ===========================================================================
+namespace race_noalloc {
+
+constexpr int64_t kMaxRows = int64_t(1) << 24;    // 16,777,216 rows
+constexpr int64_t kMaxNnz = int64_t(1) << 28;     // stored upper entries
+constexpr int kGroupRows = 256;                   // rows per counting group
+constexpr int64_t kMaxGroups = kMaxRows / kGroupRows;
+constexpr int64_t kMaxBlocks = kMaxRows / 64 + kMaxNnz / 512 + 2;
+constexpr int64_t kHeader = 64;                   // [0] status [1] blocks [2] first unsafe [3] long row
+constexpr int64_t kWords = kHeader + kMaxGroups + kMaxBlocks + 1;   // 3.4 MB in total
+
+static __device__ __align__(256) int32_t g_scratch[kWords];
+
+__device__ __forceinline__ bool starts_block(const int32_t* __restrict__ rp, int64_t r) {
+    return (r % 64 == 0) || ((__ldg(rp + r) >> 9) != (__ldg(rp + r - 1) >> 9));
+}
+
+__global__ void k_reset(int32_t* sc) {
+    if (threadIdx.x == 0) {
+        sc[0] = RACE_OK;
+        sc[1] = 0;
+        sc[2] = INT32_MAX;
+        sc[3] = 0;
+    }
+}
+
+// per 256-row group: number of block starts (one warp per group); flags any
+// row longer than 512 entries
+__global__ void k_count(int32_t n, const int32_t* __restrict__ rp, int32_t* sc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t ngroups = (static_cast<int64_t>(n) + kGroupRows - 1) / kGroupRows;
+    for (int64_t g = warp; g < ngroups; g += nwarps) {
+        int32_t cnt = 0;
+        bool longrow = false;
+        for (int k = 0; k < kGroupRows / 32; ++k) {
+            const int64_t r = g * kGroupRows + k * 32 + lane;
+            const bool f = r < n && starts_block(rp, r);
+            longrow |= r < n && (__ldg(rp + r + 1) - __ldg(rp + r)) > 512;
+            cnt += __popc(__ballot_sync(0xffffffffu, f));
+        }
+        if (__any_sync(0xffffffffu, longrow) && lane == 0) atomicExch(sc + 3, 1);
+        if (lane == 0) sc[kHeader + g] = cnt;
+    }
+}
+
+// exclusive scan of the group counts in place (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) k_scan(int32_t ngroups, int32_t* sc) {
+    __shared__ int32_t part[1024];
+    int32_t* c = sc + kHeader;
+    const int t = threadIdx.x;
+    const int32_t per = (ngroups + 1023) / 1024;
+    const int32_t beg = min(t * per, ngroups), end = min(beg + per, ngroups);
+    int32_t sum = 0;
+    for (int32_t i = beg; i < end; ++i) sum += c[i];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = part[t] - sum;
+    for (int32_t i = beg; i < end; ++i) {
+        const int32_t v = c[i];
+        c[i] = run;
+        run += v;
+    }
+    if (t == 1023) sc[1] = part[1023];
+}
+
+// block starts in row order, then the sentinel n
+__global__ void k_write(int32_t n, const int32_t* __restrict__ rp, int32_t* sc) {
+    int32_t* tbl = sc + kHeader + kMaxGroups;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t ngroups = (static_cast<int64_t>(n) + kGroupRows - 1) / kGroupRows;
+    for (int64_t g = warp; g < ngroups; g += nwarps) {
+        int32_t pos = sc[kHeader + g];
+        for (int k = 0; k < kGroupRows / 32; ++k) {
+            const int64_t r = g * kGroupRows + k * 32 + lane;
+            const bool f = r < n && starts_block(rp, r);
+            const unsigned m = __ballot_sync(0xffffffffu, f);
+            if (f) tbl[pos + __popc(m & lt)] = static_cast<int32_t>(r);
+            pos += __popc(m);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tbl[sc[1]] = n;
+}
+
+// first block whose widened copies would leave [0, nnz) or [0, n]
+__global__ void k_safe(int32_t n, int64_t nnz, const int32_t* __restrict__ rp, int32_t* sc) {
+    const int32_t* tbl = sc + kHeader + kMaxGroups;
+    const int32_t nb = sc[1];
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nb;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t r0 = tbl[i], r1 = tbl[i + 1];
+        const int64_t s = __ldg(rp + r0), e = __ldg(rp + r1);
+        const int64_t s_al = s & ~int64_t(3), n_el = ((e - s_al) + 3) & ~int64_t(3);
+        const int64_t r0_al = r0 & ~3, n_rp = ((r1 + 1 - r0_al) + 3) & ~int64_t(3);
+        if (s_al + n_el > nnz || r0_al + n_rp > int64_t(n) + 1) atomicMin(sc + 2, static_cast<int32_t>(i));
+    }
+}
+
+// rows from the first unsafe block to n: one thread per row, plain loads
+__global__ void k_tail(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, double* b, const int32_t* sc) {
+    const int32_t* tbl = sc + kHeader + kMaxGroups;
+    const int32_t first = min(sc[2], sc[1]);
+    const int32_t r_begin = tbl[first];
+    for (int64_t r = r_begin + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+         r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double xr = __ldg(x + r);
+        double acc = 0.0;
+        for (int32_t j = __ldg(rp + r); j < __ldg(rp + r + 1); ++j) {
+            const int32_t c = __ldg(col + j);
+            const double a = __ldg(val + j);
+            acc += a * __ldg(x + c);
+            if (c != r) atomicAdd(b + c, a * xr);
+        }
+        atomicAdd(b + r, acc);
+    }
+}
+
+std::mutex g_setup_mutex;
+int32_t* g_scratch_ptr[64] = {nullptr};
+int g_sm[64] = {0};
+
+}  // namespace race_noalloc
+
+extern "C" int symm_spmv_noalloc(int32_t n, int64_t nnz, const int32_t* row_ptr_d, const int32_t* col_d,
+                                 const double* val_d, const double* x_d, double* b_d, void* stream) {
+    using namespace race_noalloc;
+    if (n < 1 || nnz < n || !row_ptr_d || !col_d || !val_d || !x_d || !b_d) {
+        race_set_detail("symm_spmv_noalloc: n < 1, nnz < n or a NULL pointer");
+        return RACE_ERR_INVALID;
+    }
+    if (static_cast<const void*>(x_d) == static_cast<const void*>(b_d)) {
+        race_set_detail("symm_spmv_noalloc: x and b alias");
+        return RACE_ERR_INVALID;
+    }
+    if (n > kMaxRows || nnz > kMaxNnz) {
+        race_set_detail("symm_spmv_noalloc: at most 16,777,216 rows and 268,435,456 stored entries "
+                        "(fixed scratch of the non-allocating path)");
+        return RACE_ERR_OVERFLOW;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        race_set_detail("symm_spmv_noalloc: no usable current device");
+        return RACE_ERR_CUDA;
+    }
+    int32_t* sc = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_ptr[dev]) {
+            // first call on this device: the host-side symbol is only a stand-in,
+            // the kernels need the array's device address
+            e = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_scratch_ptr[dev]), g_scratch);
+            if (e != cudaSuccess) {
+                g_scratch_ptr[dev] = nullptr;
+                race_set_detail(std::string("symm_spmv_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+                return RACE_ERR_CUDA;
+            }
+            cudaDeviceGetAttribute(&g_sm[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (g_sm[dev] <= 0) g_sm[dev] = 1;
+        }
+        sc = g_scratch_ptr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int32_t ngroups = static_cast<int32_t>((static_cast<int64_t>(n) + kGroupRows - 1) / kGroupRows);
+    const int gw = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(ngroups) * 32 + 255) / 256, g_sm[dev] * 8));
+    e = cudaMemsetAsync(b_d, 0, sizeof(double) * static_cast<size_t>(n), st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("symm_spmv_noalloc: memset: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    k_reset<<<1, 32, 0, st>>>(sc);
+    k_count<<<gw, 256, 0, st>>>(n, row_ptr_d, sc);
+    k_scan<<<1, 1024, 0, st>>>(ngroups, sc);
+    k_write<<<gw, 256, 0, st>>>(n, row_ptr_d, sc);
+    k_safe<<<g_sm[dev] * 4, 256, 0, st>>>(n, nnz, row_ptr_d, sc);
+    int32_t head[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(head, sc, sizeof(head), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("symm_spmv_noalloc: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    if (head[3]) {
+        race_set_detail("symm_spmv_noalloc: a row has more than 512 stored entries");
+        return RACE_ERR_UNSUPPORTED;
+    }
+    const int64_t n_safe = std::min(head[2], head[1]);
+    const int32_t* tbl = sc + kHeader + kMaxGroups;
+    race_dev::launch_stream<double, race_dev::kSymmRed>(n_safe, tbl, row_ptr_d, col_d, val_d, x_d, b_d, sc, g_sm[dev],
+                                                          4, st);
+    k_tail<<<g_sm[dev] * 2, 256, 0, st>>>(n, row_ptr_d, col_d, val_d, x_d, b_d, sc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(head, sc, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("symm_spmv_noalloc: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    if (head[0] != RACE_OK) {
+        race_set_detail("symm_spmv_noalloc: a bounded device wait gave up");
+        return head[0];
+    }
+    return RACE_OK;
 }
