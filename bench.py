@@ -38,6 +38,7 @@ WORKLOAD_DESC = {
              "x~U[-1,1) seed 3, RACE-permuted",
     "st27_200": "3D 27-point stencil 200^3 nonperiodic SPD, off-diag -U(0,1] seed 4, FP64 upper CRS",
     "anderson32": "3D Anderson 32^3 periodic 7-pt, disorder U[-8.25,8.25) seed 1, FP64 upper CRS",
+    "xxz24": "Heisenberg XXZ chain L=24 periodic, Sz=0 (2,704,156 rows), FP64 upper CRS (small profiling case)",
 }
 
 
@@ -199,10 +200,12 @@ def run_ours(args):
     s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream)
     build_s = time.perf_counter() - t0
     lc = cfg["launch"]
-    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"])
+    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
+                      lc["regs_per_row"])
     fl = cfg["full_launch"]
     R.race_prepare_full(s, stream)
-    R.race_set_launch(s, 1, fl["executor"], fl["group_lanes"], fl["rows_per_group"], fl["blocks_per_sm"])
+    R.race_set_launch(s, 1, fl["executor"], fl["group_lanes"], fl["rows_per_group"], fl["blocks_per_sm"],
+                      fl["regs_per_row"])
     info = s.info()
     perm = s.perm()
     x_host = configs.vectors(name, n)

@@ -24,12 +24,15 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 
 # schedule parameters per workload: n_workers, eps, max_depth, the executor
 # tested at full size, and the launch shapes of symm_spmv / spmv_full
-_L = dict(executor=3, group_lanes=4, rows_per_group=1, blocks_per_sm=0)
-_F = dict(executor=0, group_lanes=4, rows_per_group=1, blocks_per_sm=0)
+# (shapes from the measured sweeps on GB300: one row per thread wins)
+_L = dict(executor=3, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=8)
+_LP = dict(executor=5, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4)
+_F = dict(executor=2, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=16)
 SCHEDULE = {
     "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
     "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
-    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
+    "xxz24": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
+    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_LP, full_launch=_F),
 }
 
 
