@@ -152,6 +152,20 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    i+2 in flight together); updates of b as
                                    reductions at L2                         */
 
+#define RACE_EXEC_WINDOW_RED 6  /* tiles of consecutive rows whose write set
+                                   (rows + upper targets, at most 2048) is
+                                   a shared-memory window: x staged, updates
+                                   accumulated by shared-memory atomics, then
+                                   flushed coalesced as L2 reductions       */
+#define RACE_EXEC_WINDOW_RACE 7 /* the same windows over the RACE leaves, one
+                                   launch per phase; a leaf's tiles run in
+                                   order on one block and the windows are
+                                   flushed with plain loads and stores: the
+                                   leaves of a phase are distance-2
+                                   independent, so no two blocks write one
+                                   entry of b (conflict-free, no atomics in
+                                   global memory)                           */
+
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {
     int32_t executor;        /* symm_spmv: RACE_EXEC_*; spmv_full: 0 = row

@@ -50,6 +50,8 @@ RACE_EXEC_ATOMIC = 2
 RACE_EXEC_ROWS_RED = 3
 RACE_EXEC_STREAM_RED = 4
 RACE_EXEC_PIPE_RED = 5
+RACE_EXEC_WINDOW_RED = 6
+RACE_EXEC_WINDOW_RACE = 7
 
 
 class race_launch(ctypes.Structure):

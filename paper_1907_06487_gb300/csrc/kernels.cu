@@ -533,6 +533,12 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
         race_stream_symm_red(s, x, b, st, sm_count());
     } else if (exec == RACE_EXEC_PIPE_RED) {
         launch_pipe<VT, true>(s->plan.n, s->d_rp, s->d_col, s->d_val, x, b, s->launch, st);
+    } else if (exec == RACE_EXEC_WINDOW_RED || exec == RACE_EXEC_WINDOW_RACE) {
+        const bool race_mode = exec == RACE_EXEC_WINDOW_RACE;
+        if ((race_mode ? s->win_race.ready : s->win_red.ready))
+            race_window_launch(s, race_mode, x, b, st, sm_count());
+        else  // a row longer than the window: the row-block kernel serves it
+            RACE_GU_SWITCH(launch_rows_red_gu, VT, 1, 1, s, x, b, st);
     } else {
         RACE_DISPATCH(launch_phases)
     }
@@ -628,7 +634,7 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_PIPE_RED) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_WINDOW_RACE) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -693,7 +699,8 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool g_ok = l->group_lanes == 1 || l->group_lanes == 2 || l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
-        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_PIPE_RED || l->regs_per_row < 0 || l->regs_per_row > 16 || (which != 0 && which != 1)) {
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_WINDOW_RACE || l->regs_per_row < 0 ||
+        l->regs_per_row > 16 || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
     }

@@ -32,6 +32,12 @@ void release_device(race_schedule* s) {
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
+    for (WindowSet* w : {&s->win_red, &s->win_race}) {
+        void* wp[] = {w->d_tiles, w->d_ext, w->d_lidx, w->d_unit_tile};
+        for (void* p : wp)
+            if (p) cudaFree(p);
+        *w = WindowSet();
+    }
 }
 
 // Streamed arrays get kStreamPad zeroed elements after their end so that
@@ -245,6 +251,41 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
         if (rc == RACE_OK) {
             std::vector<int32_t> z(1, 0);
             rc = upload(z, &s->d_status, st);
+        }
+        if (rc == RACE_OK && s->max_row_upper + 1 <= kWindowCap) {
+            // window executors: flat tiles over all rows, and tiles of every
+            // RACE leaf in phase order
+            const int32_t n = a->n;
+            std::vector<int32_t> mark(n, 0);
+            int32_t stamp = 0;
+            for (int mode = 0; mode < 2 && rc == RACE_OK; ++mode) {
+                WindowSet& w = mode == 0 ? s->win_red : s->win_race;
+                std::vector<int32_t> tiles, ext, unit_tile;
+                std::vector<uint16_t> lidx(s->h_col.size(), 0);
+                if (mode == 0) {
+                    race_make_tiles(s->h_rp.data(), s->h_col.data(), 0, n, kWindowCap, tiles, ext, lidx, mark, stamp);
+                } else {
+                    const auto& lo = s->plan.leaf_lo;
+                    const auto& hi = s->plan.leaf_hi;
+                    for (size_t q = 0; q < lo.size(); ++q) {
+                        unit_tile.push_back(static_cast<int32_t>(tiles.size() / 4));
+                        race_make_tiles(s->h_rp.data(), s->h_col.data(), lo[q], hi[q], kWindowCap, tiles, ext, lidx,
+                                        mark, stamp);
+                    }
+                    unit_tile.push_back(static_cast<int32_t>(tiles.size() / 4));
+                }
+                w.n_tiles = static_cast<int32_t>(tiles.size() / 4);
+                rc = upload(tiles, &w.d_tiles, st);
+                if (rc == RACE_OK) rc = upload(ext, &w.d_ext, st);
+                if (rc == RACE_OK) rc = upload(lidx, &w.d_lidx, st);
+                if (rc == RACE_OK && mode == 1) rc = upload(unit_tile, &w.d_unit_tile, st);
+                if (rc == RACE_OK) {
+                    // host vectors go out of scope: finish the copies first
+                    cudaError_t e = cudaStreamSynchronize(st);
+                    if (e != cudaSuccess) rc = cuda_fail(e, "window upload");
+                }
+                w.ready = (rc == RACE_OK);
+            }
         }
         if (rc == RACE_OK) {
             cudaError_t e = cudaStreamSynchronize(st);

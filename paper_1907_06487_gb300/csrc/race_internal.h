@@ -47,6 +47,19 @@ std::vector<uint8_t> export_plan(const Plan& plan);
 
 }  // namespace race
 
+// Capacity (entries) of the shared-memory window of the window executors.
+constexpr int32_t kWindowCap = 2048;
+
+// Device tiles of one window executor (see window_kernels.cu).
+struct WindowSet {
+    int32_t n_tiles = 0;
+    int32_t* d_tiles = nullptr;      // 4 int32 per tile: lo, hi, ext_off, ext_len
+    int32_t* d_ext = nullptr;        // external targets, sorted per tile
+    uint16_t* d_lidx = nullptr;      // local window index of every stored entry
+    int32_t* d_unit_tile = nullptr;  // RACE mode: first tile of every leaf (+1)
+    bool ready = false;
+};
+
 // The opaque handle of the C ABI.
 struct race_schedule {
     race::Plan plan;
@@ -77,6 +90,7 @@ struct race_schedule {
     int64_t n_fblk = 0;
     int32_t* d_status = nullptr;  // device status word (RACE_ERR_TIMEOUT)
     int32_t max_row_upper = 0, max_row_full = 0;
+    WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
     race_launch launch{};       // symm_spmv executor and shape
     race_launch full_launch{};  // spmv_full shape
 };
@@ -89,6 +103,13 @@ int32_t race_max_row(const int32_t* rp, int32_t n);
 // Streaming launchers (stream_kernels.cu).
 int race_stream_full(const race_schedule* s, const double* x, double* b, cudaStream_t st, int sm_count);
 int race_stream_symm_red(const race_schedule* s, const double* x, double* b, cudaStream_t st, int sm_count);
+
+// Window executors (window_kernels.cu).
+void race_make_tiles(const int32_t* rp, const int32_t* col, int32_t lo, int32_t hi, int32_t cap,
+                     std::vector<int32_t>& tiles, std::vector<int32_t>& ext, std::vector<uint16_t>& lidx,
+                     std::vector<int32_t>& mark, int32_t& stamp);
+int race_window_launch(const race_schedule* s, bool race_mode, const double* x, double* b, cudaStream_t st,
+                       int sm_count);
 
 // Error detail for race_last_error_detail (thread-local).
 void race_set_detail(const std::string& s);

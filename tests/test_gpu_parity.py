@@ -63,7 +63,7 @@ MATS = [
 ]
 
 
-@pytest.mark.parametrize("executor", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("executor", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("name,mk,nt,eps,md", MATS, ids=[m[0] for m in MATS])
 def test_symm_spmv_parity(dev, oracle_mod, matgen_mod, name, mk, nt, eps, md, executor):
     m = mk(matgen_mod)
