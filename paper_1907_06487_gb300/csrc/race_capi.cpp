@@ -33,7 +33,8 @@ void release_device(race_schedule* s) {
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
     for (WindowSet* w : {&s->win_red, &s->win_race}) {
-        void* wp[] = {w->d_tiles, w->d_ext, w->d_lidx, w->d_unit_tile};
+        void* wp[] = {w->d_hdr, w->d_ext, w->d_val, w->d_lidx, w->d_pos, w->d_slot_row, w->d_rs_pos,
+                      w->d_chunk_len, w->d_seg, w->d_unit_tile};
         for (void* p : wp)
             if (p) cudaFree(p);
         *w = WindowSet();
@@ -258,26 +259,48 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
             const int32_t n = a->n;
             std::vector<int32_t> mark(n, 0);
             int32_t stamp = 0;
+            std::vector<double> v64;
+            const double* vals = s->h_val64.data();
+            if (s->val_type == RACE_F32) {
+                v64.assign(s->h_val32.begin(), s->h_val32.end());
+                vals = v64.data();
+            }
             for (int mode = 0; mode < 2 && rc == RACE_OK; ++mode) {
                 WindowSet& w = mode == 0 ? s->win_red : s->win_race;
-                std::vector<int32_t> tiles, ext, unit_tile;
-                std::vector<uint16_t> lidx(s->h_col.size(), 0);
+                WindowHost wh;
+                std::vector<int32_t> unit_tile;
                 if (mode == 0) {
-                    race_make_tiles(s->h_rp.data(), s->h_col.data(), 0, n, kWindowCap, tiles, ext, lidx, mark, stamp);
+                    race_make_tiles(s->h_rp.data(), s->h_col.data(), vals, 0, n, wh, mark, stamp);
                 } else {
                     const auto& lo = s->plan.leaf_lo;
                     const auto& hi = s->plan.leaf_hi;
                     for (size_t q = 0; q < lo.size(); ++q) {
-                        unit_tile.push_back(static_cast<int32_t>(tiles.size() / 4));
-                        race_make_tiles(s->h_rp.data(), s->h_col.data(), lo[q], hi[q], kWindowCap, tiles, ext, lidx,
-                                        mark, stamp);
+                        unit_tile.push_back(static_cast<int32_t>(wh.hdr.size() / 8));
+                        race_make_tiles(s->h_rp.data(), s->h_col.data(), vals, lo[q], hi[q], wh, mark, stamp);
                     }
-                    unit_tile.push_back(static_cast<int32_t>(tiles.size() / 4));
+                    unit_tile.push_back(static_cast<int32_t>(wh.hdr.size() / 8));
                 }
-                w.n_tiles = static_cast<int32_t>(tiles.size() / 4);
-                rc = upload(tiles, &w.d_tiles, st);
-                if (rc == RACE_OK) rc = upload(ext, &w.d_ext, st);
-                if (rc == RACE_OK) rc = upload(lidx, &w.d_lidx, st);
+                w.n_tiles = static_cast<int32_t>(wh.hdr.size() / 8);
+                rc = upload(wh.hdr, &w.d_hdr, st);
+                if (rc == RACE_OK) rc = upload(wh.ext, &w.d_ext, st);
+                if (rc == RACE_OK) {
+                    if (s->val_type == RACE_F64) {
+                        double* d = nullptr;
+                        rc = upload(wh.val, &d, st);
+                        w.d_val = d;
+                    } else {
+                        std::vector<float> f(wh.val.begin(), wh.val.end());
+                        float* d = nullptr;
+                        rc = upload(f, &d, st);
+                        w.d_val = d;
+                    }
+                }
+                if (rc == RACE_OK) rc = upload(wh.lidx, &w.d_lidx, st);
+                if (rc == RACE_OK) rc = upload(wh.pos, &w.d_pos, st);
+                if (rc == RACE_OK) rc = upload(wh.slot_row, &w.d_slot_row, st);
+                if (rc == RACE_OK) rc = upload(wh.rs_pos, &w.d_rs_pos, st);
+                if (rc == RACE_OK) rc = upload(wh.chunk_len, &w.d_chunk_len, st);
+                if (rc == RACE_OK) rc = upload(wh.seg, &w.d_seg, st);
                 if (rc == RACE_OK && mode == 1) rc = upload(unit_tile, &w.d_unit_tile, st);
                 if (rc == RACE_OK) {
                     // host vectors go out of scope: finish the copies first

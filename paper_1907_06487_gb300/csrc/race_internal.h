@@ -47,15 +47,36 @@ std::vector<uint8_t> export_plan(const Plan& plan);
 
 }  // namespace race
 
-// Capacity (entries) of the shared-memory window of the window executors.
+// Capacities of the shared-memory windows of the window executors: write
+// set entries per tile, and contributions (row sums + transposed updates).
 constexpr int32_t kWindowCap = 2048;
+constexpr int32_t kContribCap = 4096;
 
-// Device tiles of one window executor (see window_kernels.cu).
+// Host image of the tiles of one window executor (see window_kernels.cu).
+struct WindowHost {
+    std::vector<int32_t> hdr;        // 8 int32 per tile
+    std::vector<int32_t> ext;        // external targets, sorted per tile
+    std::vector<double> val;         // entries, chunk-major (32 slots, column-major)
+    std::vector<uint16_t> lidx;      // window index of every entry (0xFFFF = padding)
+    std::vector<uint16_t> pos;       // contribution position of every off-diagonal entry
+    std::vector<uint16_t> slot_row;  // local row of every slot (0xFFFF = padding)
+    std::vector<uint16_t> rs_pos;    // contribution position of every slot's row sum
+    std::vector<uint16_t> chunk_len; // entries per slot in every chunk
+    std::vector<uint16_t> seg;       // per tile: contribution groups of the w targets (w+1)
+};
+
+// Device tiles of one window executor.
 struct WindowSet {
     int32_t n_tiles = 0;
-    int32_t* d_tiles = nullptr;      // 4 int32 per tile: lo, hi, ext_off, ext_len
-    int32_t* d_ext = nullptr;        // external targets, sorted per tile
-    uint16_t* d_lidx = nullptr;      // local window index of every stored entry
+    int32_t* d_hdr = nullptr;
+    int32_t* d_ext = nullptr;
+    void* d_val = nullptr;           // double or float, as the schedule's values
+    uint16_t* d_lidx = nullptr;
+    uint16_t* d_pos = nullptr;
+    uint16_t* d_slot_row = nullptr;
+    uint16_t* d_rs_pos = nullptr;
+    uint16_t* d_chunk_len = nullptr;
+    uint16_t* d_seg = nullptr;
     int32_t* d_unit_tile = nullptr;  // RACE mode: first tile of every leaf (+1)
     bool ready = false;
 };
@@ -105,9 +126,8 @@ int race_stream_full(const race_schedule* s, const double* x, double* b, cudaStr
 int race_stream_symm_red(const race_schedule* s, const double* x, double* b, cudaStream_t st, int sm_count);
 
 // Window executors (window_kernels.cu).
-void race_make_tiles(const int32_t* rp, const int32_t* col, int32_t lo, int32_t hi, int32_t cap,
-                     std::vector<int32_t>& tiles, std::vector<int32_t>& ext, std::vector<uint16_t>& lidx,
-                     std::vector<int32_t>& mark, int32_t& stamp);
+void race_make_tiles(const int32_t* rp, const int32_t* col, const double* val, int32_t lo, int32_t hi,
+                     WindowHost& out, std::vector<int32_t>& mark, int32_t& stamp);
 int race_window_launch(const race_schedule* s, bool race_mode, const double* x, double* b, cudaStream_t st,
                        int sm_count);
 
