@@ -236,6 +236,32 @@ int race_get_info(const race_schedule *s, race_info *info);
  * n_sublevels, n_children, phase_count, phase_offset; int64 size, neff.    */
 int race_export(const race_schedule *s, void *buf, size_t *size);
 
+/* ---- batches and tuning (spec: many matrices of uneven size in one
+ * captured graph; launch shapes picked by an autotuner) ------------------- */
+typedef struct race_batch race_batch;  /* opaque */
+
+/* race_batch_create — captures from `stream` (not the legacy default
+ * stream) one symm_spmv (k == 1) or symm_spmm (1 < k <= 16) per schedule,
+ * with the schedule's current launch shape, on the caller-owned device
+ * arrays X_d[i] / B_d[i] (n_i x k row-major, permuted order), into one CUDA
+ * graph.  The arrays must stay valid while the batch is used.  The call
+ * enqueues nothing; race_batch_launch replays the whole batch.
+ * Errors: RACE_ERR_INVALID, RACE_ERR_CUDA.                                  */
+int race_batch_create(race_schedule *const *s, int32_t count, int32_t k, const double *const *X_d,
+                      double *const *B_d, void *stream, race_batch **out);
+int race_batch_launch(race_batch *b, void *stream);
+void race_batch_free(race_batch *b);
+
+/* race_autotune — times the candidate launch shapes (executors
+ * RACE_EXEC_ROWS_RED and RACE_EXEC_PIPE_RED with their lane, row and
+ * register shapes, default and 4 blocks per SM) of symm_spmv (k == 1) or
+ * symm_spmm (k > 1) on the given buffers: one warm-up and `reps` timed
+ * calls each, CUDA events on `stream`.  Keeps the fastest as the
+ * schedule's launch shape and returns it in *best (and its time per call
+ * in microseconds in *best_us; either may be NULL).  B_d is overwritten.   */
+int race_autotune(race_schedule *s, int32_t k, const double *X_d, double *B_d, int32_t reps, void *stream,
+                  race_launch *best, float *best_us);
+
 /* symm_spmv_noalloc — b = A x like symm_spmv, for callers that must not
  * allocate device memory themselves or through this library: for example a
  * plug-in whose host application owns every device allocation, code that

@@ -42,7 +42,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_prepare_full", "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix",
             "race_get_phases", "race_get_info", "race_export", "race_free", "race_strerror",
             "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status",
-            "symm_spmv_noalloc")
+            "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -127,6 +127,15 @@ def lib():
     L.race_poll_status.restype = ctypes.c_int
     L.symm_spmv_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     L.symm_spmv_noalloc.restype = ctypes.c_int
+    pvp = ctypes.POINTER(vp)
+    L.race_batch_create.argtypes = [pvp, i32, i32, pvp, pvp, vp, pvp]
+    L.race_batch_create.restype = ctypes.c_int
+    L.race_batch_launch.argtypes = [vp, vp]
+    L.race_batch_launch.restype = ctypes.c_int
+    L.race_batch_free.argtypes = [vp]
+    L.race_batch_free.restype = None
+    L.race_autotune.argtypes = [vp, i32, vp, vp, i32, vp, ctypes.POINTER(race_launch), ctypes.POINTER(ctypes.c_float)]
+    L.race_autotune.restype = ctypes.c_int
     L.race_get_launch.restype = ctypes.c_int
     L.race_free.argtypes = [vp]
     L.race_free.restype = None
@@ -273,6 +282,49 @@ def race_get_launch(s: Schedule, which):
 
 def race_poll_status(s: Schedule, stream=None):
     _check(lib().race_poll_status(s.handle, _stream(stream)), "race_poll_status")
+
+
+class Batch:
+    """One CUDA graph replaying a SymmSpMV/SymmSpMM per schedule (race_batch_*)."""
+
+    def __init__(self, schedules, k, Xs, Bs, stream):
+        n = len(schedules)
+        if n < 1 or len(Xs) != n or len(Bs) != n:
+            raise ValueError("schedules, Xs and Bs must have the same non-zero length")
+        self._keep = (list(schedules), list(Xs), list(Bs))   # device arrays must outlive the graph
+        arr = ctypes.c_void_p * n
+        h = ctypes.c_void_p()
+        _check(lib().race_batch_create(arr(*[s.handle for s in schedules]), n, int(k), arr(*[_ptr(x) for x in Xs]),
+                                       arr(*[_ptr(b) for b in Bs]), _stream(stream), ctypes.byref(h)),
+               "race_batch_create")
+        self._h = h.value
+
+    def launch(self, stream=None):
+        _check(lib().race_batch_launch(self._h, _stream(stream)), "race_batch_launch")
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().race_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def race_batch_create(schedules, k, Xs, Bs, stream) -> Batch:
+    return Batch(schedules, k, Xs, Bs, stream)
+
+
+def race_autotune(s: Schedule, k, X, B, reps=5, stream=None):
+    """Pick the fastest launch shape for this schedule; returns (launch dict, us per call)."""
+    best = race_launch()
+    us = ctypes.c_float()
+    _check(lib().race_autotune(s.handle, int(k), _ptr(X), _ptr(B), int(reps), _stream(stream), ctypes.byref(best),
+                               ctypes.byref(us)), "race_autotune")
+    return {f: getattr(best, f) for f, _ in best._fields_}, us.value
 
 
 def symm_spmv_noalloc(n, nnz, row_ptr, col, val, x, b, stream=None):

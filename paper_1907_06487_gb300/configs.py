@@ -36,6 +36,26 @@ SCHEDULE = {
 }
 
 
+def batch64(count: int = 64, scale: float = 1.0) -> list:
+    """The batch workload: alternately 3D Anderson models with L uniform in
+    [16, 96] (disorder 16.5, per-matrix seed) and random geometric graphs with
+    n uniform in [1e4, 1e6] points (unit cube, radius for mean degree 20,
+    weights U(0,1], diag = sum + 1).  Draws from splitmix64 stream seed 6.
+    `scale` < 1 shrinks every matrix (test-sized batches)."""
+    u = matgen.uniform(2 * count, 6, 0.0, 1.0)
+    out = []
+    for i in range(count):
+        if i % 2 == 0:
+            L = 16 + int(u[i] * 81)
+            L = max(4, int(round(L * scale ** (1.0 / 3.0))))
+            out.append(dict(matgen.anderson(L, W=16.5, seed=100 + i), name=f"anderson{L}"))
+        else:
+            npts = 10000 + int(u[i] * (1000000 - 10000 + 1))
+            npts = max(200, int(npts * scale))
+            out.append(dict(matgen.geometric(npts, seed=200 + i), name=f"geometric{npts}"))
+    return out
+
+
 def matrix(name: str) -> dict:
     if name == "anderson32":
         return matgen.anderson(32, W=16.5, seed=1)

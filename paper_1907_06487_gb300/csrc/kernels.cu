@@ -399,6 +399,59 @@ __global__ void __launch_bounds__(kBlock) k_rows_pipe(int32_t n, const int32_t* 
     }
 }
 
+// SymmSpMM with K right-hand sides (row-major n x K), all rows at once: a
+// group of K lanes owns a row, lane c serves column c, so the K values of
+// a row of X or B are contiguous across the group.  Updates of B are
+// reductions at L2 (B zeroed before).  R rows per group in flight.
+template <typename VT, int K, int R>
+__global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const int32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const VT* __restrict__ val, const double* __restrict__ X,
+                                                            double* B) {
+    const int c = threadIdx.x & (K - 1);
+    const int64_t grp = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / K;
+    const int64_t ngrp = static_cast<int64_t>(gridDim.x) * kBlock / K;
+    for (int64_t r0 = grp; r0 < n; r0 += ngrp * R) {
+        int32_t js[R], je[R];
+        double xr[R], acc[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int64_t r = r0 + q * ngrp;
+            const bool v = r < n;
+            js[q] = v ? __ldg(rp + r) : 0;
+            je[q] = v ? __ldg(rp + r + 1) : 0;
+            xr[q] = v ? __ldg(X + r * K + c) : 0.0;
+            acc[q] = 0.0;
+        }
+        int32_t len = 0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) len = max(len, je[q] - js[q]);
+        for (int32_t p = 0; p < len; ++p) {
+            double a[R], xc[R];
+            int32_t cc[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const bool v = js[q] + p < je[q];
+                a[q] = v ? ldv(val + js[q] + p) : 0.0;
+                cc[q] = v ? __ldg(col + js[q] + p) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) xc[q] = cc[q] >= 0 ? __ldg(X + static_cast<int64_t>(cc[q]) * K + c) : 0.0;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (cc[q] < 0) continue;
+                acc[q] += a[q] * xc[q];
+                if (p > 0) atomicAdd(B + static_cast<int64_t>(cc[q]) * K + c, a[q] * xr[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int64_t r = r0 + q * ngrp;
+            if (r < n) atomicAdd(B + r * K + c, acc[q]);
+        }
+    }
+}
+
 __global__ void k_permute(int32_t n, int32_t k, const int32_t* __restrict__ perm, const double* __restrict__ in,
                           double* __restrict__ out, int inverse) {
     const int64_t total = static_cast<int64_t>(n) * k;
@@ -569,6 +622,29 @@ void launch_mm(const race_schedule* s, const double* X, double* B, cudaStream_t 
 
 template <typename VT>
 int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, cudaStream_t st) {
+    if (s->launch.executor >= RACE_EXEC_ATOMIC) {
+        // row-parallel SpMM with reductions (R rows per group in flight)
+        const int32_t n = s->plan.n;
+        const int R = s->launch.rows_per_group >= 4 ? 4 : (s->launch.rows_per_group >= 2 ? 2 : 1);
+        const VT* v = static_cast<const VT*>(s->d_val);
+#define RACE_MM_ROWS(KK)                                                                                       \
+    do {                                                                                                       \
+        const int g = grid_for((static_cast<int64_t>(n) * KK + R - 1) / R, s->launch.blocks_per_sm);          \
+        if (R == 4) k_symm_mm_rows_red<VT, KK, 4><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);        \
+        else if (R == 2) k_symm_mm_rows_red<VT, KK, 2><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);   \
+        else k_symm_mm_rows_red<VT, KK, 1><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);               \
+    } while (0)
+        switch (k) {
+            case 1: RACE_MM_ROWS(1); break;
+            case 2: RACE_MM_ROWS(2); break;
+            case 4: RACE_MM_ROWS(4); break;
+            case 8: RACE_MM_ROWS(8); break;
+            case 16: RACE_MM_ROWS(16); break;
+            default: return RACE_ERR_UNSUPPORTED;
+        }
+#undef RACE_MM_ROWS
+        return RACE_OK;
+    }
     switch (k) {
         case 1: launch_mm<VT, 1>(s, X, B, st); break;
         case 2: launch_mm<VT, 2>(s, X, B, st); break;
