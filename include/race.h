@@ -262,6 +262,40 @@ void race_batch_free(race_batch *b);
 int race_autotune(race_schedule *s, int32_t k, const double *X_d, double *B_d, int32_t reps, void *stream,
                   race_launch *best, float *best_us);
 
+/* ---- learned RACE-parameter predictor (north star; the paper picks the
+ * epsilon_s by a parameter study, Sec. 5.1) ------------------------------- */
+
+/* race_features — 16 FP32 features of an upper-triangle CRS (host memory,
+ * any column order within a row) describing its rows and its BFS levels
+ * from the schedule's root: see csrc/features.cpp for the list.            */
+int race_features(const race_csr_upper *a, float *feat16);
+
+/* The predictor is a 16 -> 64 -> 64 -> 3 perceptron (ReLU, linear output)
+ * mapping features to (eps_0, eps_1, depth) in scaled units.  Its
+ * parameters are one packed FP32 device array of race_mlp_param_count()
+ * floats: W1[64][16] b1[64] W2[64][64] b2[64] W3[3][64] b3[3].            */
+int32_t race_mlp_param_count(void);
+/* floats of activation scratch for a batch (z1, h1, z2, h2, y)             */
+int64_t race_mlp_act_size(int32_t batch);
+/* floats of backward scratch for a batch                                   */
+int64_t race_mlp_work_size(int32_t batch);
+
+/* race_mlp_forward — x_d: batch x 16 features (row-major); act_d: scratch
+ * of race_mlp_act_size(batch); y_d (may be NULL): batch x 3 outputs.       */
+int race_mlp_forward(const float *params_d, int32_t batch, const float *x_d, float *act_d, float *y_d, void *stream);
+
+/* race_mlp_backward — gradient of L = 1/(2 batch) sum_b sum_k w_k (y_bk -
+ * t_bk)^2 after race_mlp_forward on the same act_d.  target_d: batch x 3;
+ * out_weight_d: 3 weights w_k; grad_d: packed like the parameters;
+ * work_d: race_mlp_work_size(batch) floats; loss_terms_d: batch x 3 terms
+ * whose sum is L.                                                          */
+int race_mlp_backward(const float *params_d, int32_t batch, const float *x_d, float *act_d, const float *target_d,
+                      const float *out_weight_d, float *grad_d, float *work_d, float *loss_terms_d, void *stream);
+
+/* race_mlp_adam — one Adam step (bias-corrected, step >= 1) in place.      */
+int race_mlp_adam(float *params_d, const float *grad_d, float *m_d, float *v_d, float lr, float beta1, float beta2,
+                  float eps, int32_t step, void *stream);
+
 /* symm_spmv_noalloc — b = A x like symm_spmv, for callers that must not
  * allocate device memory themselves or through this library: for example a
  * plug-in whose host application owns every device allocation, code that

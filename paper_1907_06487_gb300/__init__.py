@@ -42,7 +42,9 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_prepare_full", "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix",
             "race_get_phases", "race_get_info", "race_export", "race_free", "race_strerror",
             "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status",
-            "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune")
+            "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
+            "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
+            "race_mlp_backward", "race_mlp_adam")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -136,6 +138,21 @@ def lib():
     L.race_batch_free.restype = None
     L.race_autotune.argtypes = [vp, i32, vp, vp, i32, vp, ctypes.POINTER(race_launch), ctypes.POINTER(ctypes.c_float)]
     L.race_autotune.restype = ctypes.c_int
+    f32 = ctypes.c_float
+    L.race_features.argtypes = [ctypes.POINTER(race_csr_upper), vp]
+    L.race_features.restype = ctypes.c_int
+    L.race_mlp_param_count.argtypes = []
+    L.race_mlp_param_count.restype = ctypes.c_int32
+    L.race_mlp_act_size.argtypes = [i32]
+    L.race_mlp_act_size.restype = ctypes.c_int64
+    L.race_mlp_work_size.argtypes = [i32]
+    L.race_mlp_work_size.restype = ctypes.c_int64
+    L.race_mlp_forward.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.race_mlp_forward.restype = ctypes.c_int
+    L.race_mlp_backward.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.race_mlp_backward.restype = ctypes.c_int
+    L.race_mlp_adam.argtypes = [vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]
+    L.race_mlp_adam.restype = ctypes.c_int
     L.race_get_launch.restype = ctypes.c_int
     L.race_free.argtypes = [vp]
     L.race_free.restype = None
@@ -325,6 +342,34 @@ def race_autotune(s: Schedule, k, X, B, reps=5, stream=None):
     _check(lib().race_autotune(s.handle, int(k), _ptr(X), _ptr(B), int(reps), _stream(stream), ctypes.byref(best),
                                ctypes.byref(us)), "race_autotune")
     return {f: getattr(best, f) for f, _ in best._fields_}, us.value
+
+
+def race_features(m, val_type=RACE_F64):
+    """16 predictor features of a matrix dict (host numpy arrays)."""
+    n = int(m["n"])
+    rp = np.ascontiguousarray(m["row_ptr"], dtype=np.int32)
+    col = np.ascontiguousarray(m["col"], dtype=np.int32)
+    val = np.ascontiguousarray(m["val"], dtype=np.float64)
+    a = race_csr_upper(n, int(rp[-1]), rp.ctypes.data, col.ctypes.data if len(col) else None,
+                       val.ctypes.data if len(val) else None, RACE_F64)
+    out = np.zeros(16, np.float32)
+    _check(lib().race_features(ctypes.byref(a), out.ctypes.data), "race_features")
+    return out
+
+
+def race_mlp_forward(params, batch, x, act, y=None, stream=None):
+    _check(lib().race_mlp_forward(_ptr(params), int(batch), _ptr(x), _ptr(act), _ptr(y), _stream(stream)),
+           "race_mlp_forward")
+
+
+def race_mlp_backward(params, batch, x, act, target, out_weight, grad, work, loss_terms, stream=None):
+    _check(lib().race_mlp_backward(_ptr(params), int(batch), _ptr(x), _ptr(act), _ptr(target), _ptr(out_weight),
+                                   _ptr(grad), _ptr(work), _ptr(loss_terms), _stream(stream)), "race_mlp_backward")
+
+
+def race_mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().race_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), float(lr), float(beta1), float(beta2),
+                               float(eps), int(step), _stream(stream)), "race_mlp_adam")
 
 
 def symm_spmv_noalloc(n, nnz, row_ptr, col, val, x, b, stream=None):
