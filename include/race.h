@@ -57,6 +57,10 @@ extern "C" {
                                    device upload (race_export / race_get_info
                                    work, compute entry points return
                                    RACE_ERR_UNSUPPORTED).  Needs no GPU.     */
+#define RACE_FLAG_NO_WINDOWS 2u /* skip building the shared-memory window
+                                   tiles (faster builds; the window
+                                   executors then fall back to
+                                   RACE_EXEC_ROWS_RED)                      */
 
 /* Upper-triangle CRS matrix in HOST memory (Sec. 3.2, Alg. "SymmSpMV"):
  * row i holds the entries (i, j) with j >= i.  Columns may come in any
@@ -119,6 +123,13 @@ void race_default_params(race_params *p, int32_t n_workers);
  * On success *out owns host and device copies until race_free.
  * Errors: RACE_ERR_INVALID, _OVERFLOW, _NOMEM, _CUDA.                      */
 int race_build(const race_csr_upper *a, const race_params *p, void *stream, race_schedule **out);
+
+/* race_upload — turns a schedule built with RACE_FLAG_HOST_ONLY into a
+ * device schedule (uploads it on `stream`, returns after the copies have
+ * completed); no-op for a device schedule.  Lets callers build schedules on
+ * many host threads or processes and use the GPU only for the upload.
+ * Errors: RACE_ERR_NOMEM, RACE_ERR_CUDA (the schedule stays host-only).    */
+int race_upload(race_schedule *s, void *stream);
 
 /* symm_spmv — b = A x for the symmetric A whose upper triangle was given,
  * i.e. b = A_u x + A_u^T x - diag(A) x (Alg. "SymmSpMV"), run phase by

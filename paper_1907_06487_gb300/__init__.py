@@ -34,6 +34,7 @@ RACE_F32 = 1
 RACE_BAL_ROWS = 0
 RACE_BAL_NNZ = 1
 RACE_FLAG_HOST_ONLY = 1
+RACE_FLAG_NO_WINDOWS = 2
 
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
@@ -44,7 +45,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status",
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
-            "race_mlp_backward", "race_mlp_adam")
+            "race_mlp_backward", "race_mlp_adam", "race_upload")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -139,6 +140,8 @@ def lib():
     L.race_autotune.argtypes = [vp, i32, vp, vp, i32, vp, ctypes.POINTER(race_launch), ctypes.POINTER(ctypes.c_float)]
     L.race_autotune.restype = ctypes.c_int
     f32 = ctypes.c_float
+    L.race_upload.argtypes = [vp, vp]
+    L.race_upload.restype = ctypes.c_int
     L.race_features.argtypes = [ctypes.POINTER(race_csr_upper), vp]
     L.race_features.restype = ctypes.c_int
     L.race_mlp_param_count.argtypes = []
@@ -193,7 +196,8 @@ def _check(rc, where):
         raise RaceError(rc, where)
 
 
-def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False):
+def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False,
+                windows=True):
     p = race_params()
     lib().race_default_params(ctypes.byref(p), int(n_workers))
     e = list(eps) + [eps[-1]] * (8 - len(eps))
@@ -202,7 +206,7 @@ def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, g
     p.max_depth = int(max_depth)
     p.balance = int(balance)
     p.group_lanes = int(group_lanes)
-    p.flags = RACE_FLAG_HOST_ONLY if host_only else 0
+    p.flags = (RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
     return p
 
 
@@ -266,7 +270,7 @@ class Schedule:
 
 
 def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
-               host_only=False, stream=None, val_type=RACE_F64) -> Schedule:
+               host_only=False, stream=None, val_type=RACE_F64, windows=True) -> Schedule:
     """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
     n = int(m["n"])
     rp = np.ascontiguousarray(m["row_ptr"], dtype=np.int32)
@@ -274,7 +278,7 @@ def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS,
     val = np.ascontiguousarray(m["val"], dtype=np.float64 if val_type == RACE_F64 else np.float32)
     a = race_csr_upper(n, int(rp[-1]) if n > 0 else 0, rp.ctypes.data, col.ctypes.data if len(col) else None,
                        val.ctypes.data if len(val) else None, int(val_type))
-    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only)
+    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows)
     h = ctypes.c_void_p()
     _check(lib().race_build(ctypes.byref(a), ctypes.byref(p), _stream(stream), ctypes.byref(h)), "race_build")
     return Schedule(h.value, n)
@@ -342,6 +346,10 @@ def race_autotune(s: Schedule, k, X, B, reps=5, stream=None):
     _check(lib().race_autotune(s.handle, int(k), _ptr(X), _ptr(B), int(reps), _stream(stream), ctypes.byref(best),
                                ctypes.byref(us)), "race_autotune")
     return {f: getattr(best, f) for f, _ in best._fields_}, us.value
+
+
+def race_upload(s: Schedule, stream=None):
+    _check(lib().race_upload(s.handle, _stream(stream)), "race_upload")
 
 
 def race_features(m, val_type=RACE_F64):

@@ -163,6 +163,104 @@ int32_t race_max_row(const int32_t* rp, int32_t n) {
     return m;
 }
 
+// Device half of race_build (and of race_upload): uploads the permuted
+// matrix and schedule, builds the row blocks and the window tiles.
+static int upload_schedule(race_schedule* s, cudaStream_t st) {
+    int rc = RACE_OK;
+    const int32_t n_rows = s->plan.n;
+    
+    cudaGetDevice(&s->device);
+    if ((rc = upload(s->h_rp, &s->d_rp, st)) || (rc = upload(s->h_col, &s->d_col, st)) ||
+        (rc = upload(s->plan.leaf_lo, &s->d_leaf_lo, st)) || (rc = upload(s->plan.leaf_hi, &s->d_leaf_hi, st)) ||
+        (rc = upload(s->plan.perm, &s->d_perm, st))) {
+        return rc;
+    }
+    if (s->val_type == RACE_F64) {
+        double* d = nullptr;
+        rc = upload(s->h_val64, &d, st);
+        s->d_val = d;
+    } else {
+        float* d = nullptr;
+        rc = upload(s->h_val32, &d, st);
+        s->d_val = d;
+    }
+    if (rc == RACE_OK) {
+        std::vector<int32_t> blk = race_row_blocks(s->h_rp.data(), n_rows, 1024, 256);
+        s->n_blk = static_cast<int64_t>(blk.size()) - 1;
+        s->max_row_upper = race_max_row(s->h_rp.data(), n_rows);
+        rc = upload(blk, &s->d_blk, st);
+    }
+    if (rc == RACE_OK) {
+        std::vector<int32_t> z(1, 0);
+        rc = upload(z, &s->d_status, st);
+    }
+    if (rc == RACE_OK && s->max_row_upper + 1 <= kWindowCap && s->want_windows) {
+        // window executors: flat tiles over all rows, and tiles of every
+        // RACE leaf in phase order
+        const int32_t n = n_rows;
+        std::vector<int32_t> mark(n, 0);
+        int32_t stamp = 0;
+        std::vector<double> v64;
+        const double* vals = s->h_val64.data();
+        if (s->val_type == RACE_F32) {
+            v64.assign(s->h_val32.begin(), s->h_val32.end());
+            vals = v64.data();
+        }
+        for (int mode = 0; mode < 2 && rc == RACE_OK; ++mode) {
+            WindowSet& w = mode == 0 ? s->win_red : s->win_race;
+            WindowHost wh;
+            std::vector<int32_t> unit_tile;
+            if (mode == 0) {
+                race_make_tiles(s->h_rp.data(), s->h_col.data(), vals, 0, n, wh, mark, stamp);
+            } else {
+                const auto& lo = s->plan.leaf_lo;
+                const auto& hi = s->plan.leaf_hi;
+                for (size_t q = 0; q < lo.size(); ++q) {
+                    unit_tile.push_back(static_cast<int32_t>(wh.hdr.size() / 8));
+                    race_make_tiles(s->h_rp.data(), s->h_col.data(), vals, lo[q], hi[q], wh, mark, stamp);
+                }
+                unit_tile.push_back(static_cast<int32_t>(wh.hdr.size() / 8));
+            }
+            w.n_tiles = static_cast<int32_t>(wh.hdr.size() / 8);
+            rc = upload(wh.hdr, &w.d_hdr, st);
+            if (rc == RACE_OK) rc = upload(wh.ext, &w.d_ext, st);
+            if (rc == RACE_OK) {
+                if (s->val_type == RACE_F64) {
+                    double* d = nullptr;
+                    rc = upload(wh.val, &d, st);
+                    w.d_val = d;
+                } else {
+                    std::vector<float> f(wh.val.begin(), wh.val.end());
+                    float* d = nullptr;
+                    rc = upload(f, &d, st);
+                    w.d_val = d;
+                }
+            }
+            if (rc == RACE_OK) rc = upload(wh.lidx, &w.d_lidx, st);
+            if (rc == RACE_OK) rc = upload(wh.pos, &w.d_pos, st);
+            if (rc == RACE_OK) rc = upload(wh.slot_row, &w.d_slot_row, st);
+            if (rc == RACE_OK) rc = upload(wh.rs_pos, &w.d_rs_pos, st);
+            if (rc == RACE_OK) rc = upload(wh.chunk_len, &w.d_chunk_len, st);
+            if (rc == RACE_OK) rc = upload(wh.seg, &w.d_seg, st);
+            if (rc == RACE_OK && mode == 1) rc = upload(unit_tile, &w.d_unit_tile, st);
+            if (rc == RACE_OK) {
+                // host vectors go out of scope: finish the copies first
+                cudaError_t e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) rc = cuda_fail(e, "window upload");
+            }
+            w.ready = (rc == RACE_OK);
+        }
+    }
+    if (rc == RACE_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "upload");
+    }
+    if (rc != RACE_OK) {
+        return rc;
+    }
+    return rc;
+}
+
 extern "C" {
 
 void race_default_params(race_params* p, int32_t n_workers) {
@@ -224,96 +322,9 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
         delete s;
         return fail(RACE_ERR_NOMEM, "host allocation during build");
     }
+    s->want_windows = (p->flags & RACE_FLAG_NO_WINDOWS) ? 0 : 1;
     if (!s->host_only) {
-        cudaStream_t st = static_cast<cudaStream_t>(stream);
-        cudaGetDevice(&s->device);
-        if ((rc = upload(s->h_rp, &s->d_rp, st)) || (rc = upload(s->h_col, &s->d_col, st)) ||
-            (rc = upload(s->plan.leaf_lo, &s->d_leaf_lo, st)) || (rc = upload(s->plan.leaf_hi, &s->d_leaf_hi, st)) ||
-            (rc = upload(s->plan.perm, &s->d_perm, st))) {
-            release_device(s);
-            delete s;
-            return rc;
-        }
-        if (s->val_type == RACE_F64) {
-            double* d = nullptr;
-            rc = upload(s->h_val64, &d, st);
-            s->d_val = d;
-        } else {
-            float* d = nullptr;
-            rc = upload(s->h_val32, &d, st);
-            s->d_val = d;
-        }
-        if (rc == RACE_OK) {
-            std::vector<int32_t> blk = race_row_blocks(s->h_rp.data(), a->n, 1024, 256);
-            s->n_blk = static_cast<int64_t>(blk.size()) - 1;
-            s->max_row_upper = race_max_row(s->h_rp.data(), a->n);
-            rc = upload(blk, &s->d_blk, st);
-        }
-        if (rc == RACE_OK) {
-            std::vector<int32_t> z(1, 0);
-            rc = upload(z, &s->d_status, st);
-        }
-        if (rc == RACE_OK && s->max_row_upper + 1 <= kWindowCap) {
-            // window executors: flat tiles over all rows, and tiles of every
-            // RACE leaf in phase order
-            const int32_t n = a->n;
-            std::vector<int32_t> mark(n, 0);
-            int32_t stamp = 0;
-            std::vector<double> v64;
-            const double* vals = s->h_val64.data();
-            if (s->val_type == RACE_F32) {
-                v64.assign(s->h_val32.begin(), s->h_val32.end());
-                vals = v64.data();
-            }
-            for (int mode = 0; mode < 2 && rc == RACE_OK; ++mode) {
-                WindowSet& w = mode == 0 ? s->win_red : s->win_race;
-                WindowHost wh;
-                std::vector<int32_t> unit_tile;
-                if (mode == 0) {
-                    race_make_tiles(s->h_rp.data(), s->h_col.data(), vals, 0, n, wh, mark, stamp);
-                } else {
-                    const auto& lo = s->plan.leaf_lo;
-                    const auto& hi = s->plan.leaf_hi;
-                    for (size_t q = 0; q < lo.size(); ++q) {
-                        unit_tile.push_back(static_cast<int32_t>(wh.hdr.size() / 8));
-                        race_make_tiles(s->h_rp.data(), s->h_col.data(), vals, lo[q], hi[q], wh, mark, stamp);
-                    }
-                    unit_tile.push_back(static_cast<int32_t>(wh.hdr.size() / 8));
-                }
-                w.n_tiles = static_cast<int32_t>(wh.hdr.size() / 8);
-                rc = upload(wh.hdr, &w.d_hdr, st);
-                if (rc == RACE_OK) rc = upload(wh.ext, &w.d_ext, st);
-                if (rc == RACE_OK) {
-                    if (s->val_type == RACE_F64) {
-                        double* d = nullptr;
-                        rc = upload(wh.val, &d, st);
-                        w.d_val = d;
-                    } else {
-                        std::vector<float> f(wh.val.begin(), wh.val.end());
-                        float* d = nullptr;
-                        rc = upload(f, &d, st);
-                        w.d_val = d;
-                    }
-                }
-                if (rc == RACE_OK) rc = upload(wh.lidx, &w.d_lidx, st);
-                if (rc == RACE_OK) rc = upload(wh.pos, &w.d_pos, st);
-                if (rc == RACE_OK) rc = upload(wh.slot_row, &w.d_slot_row, st);
-                if (rc == RACE_OK) rc = upload(wh.rs_pos, &w.d_rs_pos, st);
-                if (rc == RACE_OK) rc = upload(wh.chunk_len, &w.d_chunk_len, st);
-                if (rc == RACE_OK) rc = upload(wh.seg, &w.d_seg, st);
-                if (rc == RACE_OK && mode == 1) rc = upload(unit_tile, &w.d_unit_tile, st);
-                if (rc == RACE_OK) {
-                    // host vectors go out of scope: finish the copies first
-                    cudaError_t e = cudaStreamSynchronize(st);
-                    if (e != cudaSuccess) rc = cuda_fail(e, "window upload");
-                }
-                w.ready = (rc == RACE_OK);
-            }
-        }
-        if (rc == RACE_OK) {
-            cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "upload");
-        }
+        rc = upload_schedule(s, static_cast<cudaStream_t>(stream));
         if (rc != RACE_OK) {
             release_device(s);
             delete s;
@@ -321,6 +332,19 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
         }
     }
     *out = s;
+    return RACE_OK;
+}
+
+int race_upload(race_schedule* s, void* stream) {
+    if (!s) return fail(RACE_ERR_INVALID, "NULL schedule");
+    if (!s->host_only) return RACE_OK;
+    cudaGetDevice(&s->device);
+    int rc = upload_schedule(s, static_cast<cudaStream_t>(stream));
+    if (rc != RACE_OK) {
+        release_device(s);
+        return rc;
+    }
+    s->host_only = 0;
     return RACE_OK;
 }
 

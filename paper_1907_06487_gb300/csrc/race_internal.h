@@ -87,6 +87,7 @@ struct race_schedule {
     int32_t val_type = RACE_F64;
     int32_t group_lanes = 8;
     int32_t host_only = 0;
+    int32_t want_windows = 1;
     // permuted upper CRS, host copies
     std::vector<int32_t> h_rp, h_col;
     std::vector<double> h_val64;
