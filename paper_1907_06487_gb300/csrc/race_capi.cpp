@@ -34,7 +34,7 @@ void release_device(race_schedule* s) {
     s->d_val = s->d_fval = nullptr;
     for (WindowSet* w : {&s->win_red, &s->win_race}) {
         void* wp[] = {w->d_hdr, w->d_ext, w->d_val, w->d_lidx, w->d_pos, w->d_slot_row, w->d_rs_pos,
-                      w->d_chunk_len, w->d_seg, w->d_unit_tile};
+                      w->d_chunk_off, w->d_seg, w->d_unit_tile};
         for (void* p : wp)
             if (p) cudaFree(p);
         *w = WindowSet();
@@ -240,7 +240,7 @@ static int upload_schedule(race_schedule* s, cudaStream_t st) {
             if (rc == RACE_OK) rc = upload(wh.pos, &w.d_pos, st);
             if (rc == RACE_OK) rc = upload(wh.slot_row, &w.d_slot_row, st);
             if (rc == RACE_OK) rc = upload(wh.rs_pos, &w.d_rs_pos, st);
-            if (rc == RACE_OK) rc = upload(wh.chunk_len, &w.d_chunk_len, st);
+            if (rc == RACE_OK) rc = upload(wh.chunk_off, &w.d_chunk_off, st);
             if (rc == RACE_OK) rc = upload(wh.seg, &w.d_seg, st);
             if (rc == RACE_OK && mode == 1) rc = upload(unit_tile, &w.d_unit_tile, st);
             if (rc == RACE_OK) {

@@ -61,7 +61,7 @@ struct WindowHost {
     std::vector<uint16_t> pos;       // contribution position of every off-diagonal entry
     std::vector<uint16_t> slot_row;  // local row of every slot (0xFFFF = padding)
     std::vector<uint16_t> rs_pos;    // contribution position of every slot's row sum
-    std::vector<uint16_t> chunk_len; // entries per slot in every chunk
+    std::vector<int32_t> chunk_off;  // first entry of every chunk (+ final end)
     std::vector<uint16_t> seg;       // per tile: contribution groups of the w targets (w+1)
 };
 
@@ -75,7 +75,7 @@ struct WindowSet {
     uint16_t* d_pos = nullptr;
     uint16_t* d_slot_row = nullptr;
     uint16_t* d_rs_pos = nullptr;
-    uint16_t* d_chunk_len = nullptr;
+    int32_t* d_chunk_off = nullptr;
     uint16_t* d_seg = nullptr;
     int32_t* d_unit_tile = nullptr;  // RACE mode: first tile of every leaf (+1)
     bool ready = false;

@@ -41,11 +41,12 @@
 
 namespace race_win {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr uint16_t kPadIdx = 0xFFFF;
 
-// Tile header: 8 int32 per tile.
-enum : int { kLo = 0, kHi, kExtOff, kExtLen, kEntOff, kSlotOff, kSegOff, kNChunk };
+// Tile header: 8 int32 per tile.  kChunkOff indexes chunk_off, whose entry
+// c is the first stored entry of chunk c (the next entry closes it).
+enum : int { kLo = 0, kHi, kExtOff, kExtLen, kChunkOff, kSlotOff, kSegOff, kNChunk };
 
 template <typename VT>
 __device__ __forceinline__ double ldv(const VT* p) {
@@ -57,71 +58,84 @@ __global__ void __launch_bounds__(kThreads) k_window(
     int32_t n_units, const int32_t* __restrict__ unit_tile, const int32_t* __restrict__ hdr,
     const int32_t* __restrict__ ext, const VT* __restrict__ val, const uint16_t* __restrict__ lidx,
     const uint16_t* __restrict__ pos, const uint16_t* __restrict__ slot_row, const uint16_t* __restrict__ rs_pos,
-    const uint16_t* __restrict__ chunk_len, const uint16_t* __restrict__ seg, const double* __restrict__ x,
+    const int32_t* __restrict__ chunk_off, const uint16_t* __restrict__ seg, const double* __restrict__ x,
     double* b) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* sx = reinterpret_cast<double*>(smem);
     double* sc = sx + kWindowCap;  // contribution buffer
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kPer = kWindowCap / kThreads;  // window entries per thread
     for (int32_t u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int32_t t0 = RACE ? __ldg(unit_tile + u) : u;
         const int32_t t1 = RACE ? __ldg(unit_tile + u + 1) : u + 1;
         for (int32_t t = t0; t < t1; ++t) {
             const int32_t* h = hdr + 8 * static_cast<int64_t>(t);
             const int32_t lo = __ldg(h + kLo), hi = __ldg(h + kHi), eoff = __ldg(h + kExtOff);
-            const int32_t elen = __ldg(h + kExtLen), ent = __ldg(h + kEntOff), soff = __ldg(h + kSlotOff);
+            const int32_t elen = __ldg(h + kExtLen), coff = __ldg(h + kChunkOff), soff = __ldg(h + kSlotOff);
             const int32_t goff = __ldg(h + kSegOff), nch = __ldg(h + kNChunk);
             const int32_t nr = hi - lo, w = nr + elen;
-            __syncthreads();  // the previous tile is flushed
-            for (int32_t i = tid; i < w; i += kThreads) sx[i] = __ldg(x + (i < nr ? lo + i : __ldg(ext + eoff + i - nr)));
+            // 1. stage x[W]: every index load first, then every x load
+            int32_t gi[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int32_t i = tid + q * kThreads;
+                gi[q] = i < nr ? lo + i : (i < w ? __ldg(ext + eoff + i - nr) : -1);
+            }
+            double xv[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) xv[q] = gi[q] >= 0 ? __ldg(x + gi[q]) : 0.0;
+            __syncthreads();  // the previous tile's window is flushed
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)
+                if (gi[q] >= 0) sx[tid + q * kThreads] = xv[q];
             __syncthreads();
-            // chunks of 32 slots; entry offsets accumulate over the chunks
-            int32_t cbase = ent;
-            int32_t q = 0;
+            // 2. one warp per chunk of 32 row slots, four entries per lane in flight
             for (int32_t k = warp; k < nch; k += kThreads / 32) {
-                // entry base of chunk k: sum of 32*len over chunks before it
-                for (; q < k; ++q) cbase += 32 * __ldg(chunk_len + soff / 32 + q);
-                const int32_t len = __ldg(chunk_len + soff / 32 + k);
+                const int32_t c0 = __ldg(chunk_off + coff + k), c1 = __ldg(chunk_off + coff + k + 1);
+                const int32_t len = (c1 - c0) >> 5;
                 const int32_t slot = soff + k * 32 + lane;
                 const uint16_t lr = __ldg(slot_row + slot);
+                const uint16_t rsp = __ldg(rs_pos + slot);
                 const double xr = lr != kPadIdx ? sx[lr] : 0.0;
                 double acc = 0.0;
-                int32_t p = 0;
-                for (; p + 2 <= len; p += 2) {
-                    const int64_t e0 = cbase + static_cast<int64_t>(p) * 32 + lane, e1 = e0 + 32;
-                    const double a0 = ldv(val + e0), a1 = ldv(val + e1);
-                    const uint16_t l0 = __ldg(lidx + e0), l1 = __ldg(lidx + e1);
-                    const uint16_t p0 = __ldg(pos + e0), p1 = __ldg(pos + e1);
-                    if (l0 != kPadIdx) {
-                        acc += a0 * sx[l0];
-                        if (p > 0) sc[p0] = a0 * xr;
+                for (int32_t p = 0; p < len; p += 4) {
+                    double a[4];
+                    uint16_t l[4], ps[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool v = p + q < len;
+                        const int64_t e = c0 + static_cast<int64_t>(p + q) * 32 + lane;
+                        a[q] = v ? ldv(val + e) : 0.0;
+                        l[q] = v ? __ldg(lidx + e) : kPadIdx;
+                        ps[q] = v ? __ldg(pos + e) : 0;
                     }
-                    if (l1 != kPadIdx) {
-                        acc += a1 * sx[l1];
-                        sc[p1] = a1 * xr;
-                    }
-                }
-                if (p < len) {
-                    const int64_t e0 = cbase + static_cast<int64_t>(p) * 32 + lane;
-                    const double a0 = ldv(val + e0);
-                    const uint16_t l0 = __ldg(lidx + e0), p0 = __ldg(pos + e0);
-                    if (l0 != kPadIdx) {
-                        acc += a0 * sx[l0];
-                        if (p > 0) sc[p0] = a0 * xr;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (l[q] == kPadIdx) continue;
+                        acc += a[q] * sx[l[q]];
+                        if (p + q > 0) sc[ps[q]] = a[q] * xr;  // entry 0 is the diagonal
                     }
                 }
-                if (lr != kPadIdx) sc[__ldg(rs_pos + slot)] = acc;
+                if (lr != kPadIdx) sc[rsp] = acc;
             }
             __syncthreads();
-            for (int32_t i = tid; i < w; i += kThreads) {
-                const int32_t a = __ldg(seg + goff + i), z = __ldg(seg + goff + i + 1);
+            // 3. flush: one thread per window entry, all segment bounds loaded first
+            int32_t sa[kPer], sz[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int32_t i = tid + q * kThreads;
+                sa[q] = i < w ? __ldg(seg + goff + i) : 0;
+                sz[q] = i < w ? __ldg(seg + goff + i + 1) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                if (gi[q] < 0) continue;
                 double v = 0.0;
-                for (int32_t j = a; j < z; ++j) v += sc[j];
-                const int32_t g = i < nr ? lo + i : __ldg(ext + eoff + i - nr);
+                for (int32_t j = sa[q]; j < sz[q]; ++j) v += sc[j];
                 if (RACE) {
-                    b[g] += v;
+                    b[gi[q]] += v;
                 } else {
-                    atomicAdd(b + g, v);
+                    atomicAdd(b + gi[q], v);
                 }
             }
         }
@@ -208,7 +222,8 @@ void race_make_tiles(const int32_t* rp, const int32_t* col, const double* val, i
         out.hdr.push_back(thi);
         out.hdr.push_back(static_cast<int32_t>(out.ext.size()));
         out.hdr.push_back(static_cast<int32_t>(ext.size()));
-        out.hdr.push_back(static_cast<int32_t>(out.val.size()));
+        if (out.chunk_off.empty()) out.chunk_off.push_back(0);
+        out.hdr.push_back(static_cast<int32_t>(out.chunk_off.size()) - 1);
         out.hdr.push_back(static_cast<int32_t>(out.slot_row.size()));
         out.hdr.push_back(static_cast<int32_t>(seg_off));
         out.hdr.push_back(nch);
@@ -220,8 +235,8 @@ void race_make_tiles(const int32_t* rp, const int32_t* col, const double* val, i
                 const int32_t q = k * 32 + s;
                 if (q < nr) len = std::max(len, rp[tlo + slots[q] + 1] - rp[tlo + slots[q]]);
             }
-            out.chunk_len.push_back(static_cast<uint16_t>(len));
             const size_t base = out.val.size();
+            out.chunk_off.push_back(static_cast<int32_t>(base + static_cast<size_t>(len) * 32));
             out.val.resize(base + static_cast<size_t>(len) * 32, 0.0);
             out.lidx.resize(base + static_cast<size_t>(len) * 32, kPadIdx);
             out.pos.resize(base + static_cast<size_t>(len) * 32, 0);
@@ -245,8 +260,6 @@ void race_make_tiles(const int32_t* rp, const int32_t* col, const double* val, i
                 }
             }
         }
-        // the slot table is padded to whole chunks already; keep chunk_len
-        // indexable as slot_off / 32 + k
     }
 }
 
@@ -261,12 +274,12 @@ int race_window_launch(const race_schedule* s, bool race_mode, const double* x, 
             if (race_mode) configure<double, true>(); else configure<double, false>();
             auto k = race_mode ? k_window<double, true> : k_window<double, false>;
             k<<<grid, kThreads, smem, st>>>(n_units, unit_tile, w.d_hdr, w.d_ext, static_cast<const double*>(w.d_val),
-                                           w.d_lidx, w.d_pos, w.d_slot_row, w.d_rs_pos, w.d_chunk_len, w.d_seg, x, b);
+                                           w.d_lidx, w.d_pos, w.d_slot_row, w.d_rs_pos, w.d_chunk_off, w.d_seg, x, b);
         } else {
             if (race_mode) configure<float, true>(); else configure<float, false>();
             auto k = race_mode ? k_window<float, true> : k_window<float, false>;
             k<<<grid, kThreads, smem, st>>>(n_units, unit_tile, w.d_hdr, w.d_ext, static_cast<const float*>(w.d_val),
-                                           w.d_lidx, w.d_pos, w.d_slot_row, w.d_rs_pos, w.d_chunk_len, w.d_seg, x, b);
+                                           w.d_lidx, w.d_pos, w.d_slot_row, w.d_rs_pos, w.d_chunk_off, w.d_seg, x, b);
         }
     };
     if (!race_mode) {
