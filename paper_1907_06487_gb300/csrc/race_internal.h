@@ -49,8 +49,8 @@ std::vector<uint8_t> export_plan(const Plan& plan);
 
 // Capacities of the shared-memory windows of the window executors: write
 // set entries per tile, and contributions (row sums + transposed updates).
-constexpr int32_t kWindowCap = 2048;
-constexpr int32_t kContribCap = 4096;
+constexpr int32_t kWindowCap = 1024;
+constexpr int32_t kContribCap = 2048;
 
 // Host image of the tiles of one window executor (see window_kernels.cu).
 struct WindowHost {

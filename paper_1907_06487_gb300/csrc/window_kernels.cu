@@ -41,7 +41,7 @@
 
 namespace race_win {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 128;
 constexpr uint16_t kPadIdx = 0xFFFF;
 
 // Tile header: 8 int32 per tile.  kChunkOff indexes chunk_off, whose entry
@@ -268,7 +268,7 @@ int race_window_launch(const race_schedule* s, bool race_mode, const double* x, 
     using namespace race_win;
     const WindowSet& w = race_mode ? s->win_race : s->win_red;
     const size_t smem = smem_bytes();
-    const int per_sm = s->launch.blocks_per_sm > 0 ? s->launch.blocks_per_sm : 4;
+    const int per_sm = s->launch.blocks_per_sm > 0 ? s->launch.blocks_per_sm : 9;
     auto go = [&](int32_t n_units, const int32_t* unit_tile, int grid) {
         if (s->val_type == RACE_F64) {
             if (race_mode) configure<double, true>(); else configure<double, false>();
