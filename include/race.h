@@ -176,6 +176,28 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    independent, so no two blocks write one
                                    entry of b (conflict-free, no atomics in
                                    global memory)                           */
+#define RACE_EXEC_DF64_RED  8   /* as ROWS_RED (group_lanes lanes per row):
+                                   FP64 row sums, and every transposed
+                                   update a_ij x_i formed in double-float
+                                   arithmetic on the FP32 and integer pipes
+                                   (relative error below 2^-44 each; the
+                                   result stays within 1e-12 sum_j
+                                   |a_ij x_j| of the exact one).  First use
+                                   checks the off-diagonal values once and
+                                   returns RACE_ERR_UNSUPPORTED if one is
+                                   nonzero and outside [2^-50, 2^51) in
+                                   magnitude; rows whose x_i lies outside
+                                   that range scatter in FP64.              */
+#define RACE_EXEC_SELL_DF64 9   /* the arithmetic of DF64_RED on a SELL-32-
+                                   sigma copy of the permuted upper matrix
+                                   (chunks of 32 rows stored column by
+                                   column, rows sorted by length within
+                                   windows of 1024): one warp per chunk, one
+                                   lane per row, coalesced value and column
+                                   loads.  First use builds and uploads the
+                                   copy (about the matrix's size again);
+                                   regs_per_row = entries per lane and step
+                                   (4, 8 or 16).                            */
 
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {

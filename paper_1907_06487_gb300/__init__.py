@@ -55,6 +55,8 @@ RACE_EXEC_STREAM_RED = 4
 RACE_EXEC_PIPE_RED = 5
 RACE_EXEC_WINDOW_RED = 6
 RACE_EXEC_WINDOW_RACE = 7
+RACE_EXEC_DF64_RED = 8
+RACE_EXEC_SELL_DF64 = 9
 
 
 class race_launch(ctypes.Structure):

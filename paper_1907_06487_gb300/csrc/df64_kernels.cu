@@ -1,0 +1,221 @@
+// SymmSpMV with the transposed products on the FP32 and integer pipes
+// (executor RACE_EXEC_DF64_RED).
+//
+// GB300 runs FP64 at about 1/70 of its FP32 rate.  The FP64 SymmSpMV (Alg.
+// "SymmSpMV") issues one FP64 multiply-add per stored upper entry for the row
+// sums and one FP64 multiply per off-diagonal entry for the transposed part:
+// on the 4-body XXZ Hamiltonian (26 sites) 151 M FP64 operations, 0.30 ms at
+// the measured 0.5 T/s, against 0.17 ms of HBM traffic.  Here the row sums
+// stay exact FP64 multiply-adds (80.7 M, 0.16 ms of FP64 pipe) and each
+// transposed update a_ij x_i is formed in double-float arithmetic
+// (df64.cuh): a_ij split with integer operations, x_i split once per row,
+// Dekker's product on the FP32 pipe, and the pair reassembled into a double
+// with integer operations before its reduction at L2.  b, x and the stored
+// values stay FP64.
+//
+// Accuracy: every transposed update carries a relative error below 2^-44
+// (split, product and reassembly; checked exhaustively against rational
+// arithmetic by the CPU tests), so |b_i - exact| stays below
+// (2^-44 + n_i 2^-53) sum_j |a_ij x_j| for any row length: inside
+// 1e-12 sum_j |a_ij x_j|.  Rows whose x_i is zero contribute no updates;
+// rows whose x_i lies outside the split's range [2^-50, 2^51) scatter in
+// FP64.  Stored off-diagonal values must be zero or inside that range
+// (checked once when the executor is prepared).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+
+#include "df64.cuh"
+#include "race_internal.h"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int G>
+__device__ __forceinline__ unsigned lane_mask() {
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+__device__ __forceinline__ bool out_of_range(double v) {
+    float h, l;
+    return df64::split(v, h, l) != 0;
+}
+__device__ __forceinline__ bool out_of_range(float v) {
+    const uint32_t u = __float_as_uint(v);
+    const int e = static_cast<int>((u >> 23) & 0xFFu) - 127;
+    return (u << 1) != 0 && (e < df64::kEmin || e > df64::kEmax);
+}
+
+// Sets *bad when a stored off-diagonal value is nonzero and outside the
+// split's range (one thread per row).
+template <typename VT>
+__global__ void k_check_offdiag(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const VT* __restrict__ val, int32_t* bad) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int32_t hi = __ldg(rp + r + 1);
+        for (int32_t j = __ldg(rp + r); j < hi; ++j)
+            if (__ldg(col + j) != r && out_of_range(__ldg(val + j))) *bad = 1;
+    }
+}
+
+
+// How a row scatters its transposed part.
+enum Scatter { kSplit = 0, kFp64 = 1, kNone = 2 };
+
+// One row's share of one lane: FP64 row sum returned, transposed updates
+// sent to b.  Four independent entries per lane and iteration.
+template <typename VT, int G, int MODE>
+__device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, int lane,
+                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                           const double* __restrict__ x, double* b, double xr, float xrh,
+                                           float xrl) {
+    double acc = 0.0;
+    for (int32_t idx = lo + lane; idx < hi; idx += 4 * G) {
+        VT a[4];
+        int32_t c[4];
+        double xc[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int32_t j = idx + t * G;
+            const bool v = j < hi;
+            a[t] = v ? __ldg(val + j) : VT(0);
+            c[t] = v ? __ldg(col + j) : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) xc[t] = c[t] >= 0 ? __ldg(x + c[t]) : 0.0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (c[t] < 0) continue;
+            acc = fma(static_cast<double>(a[t]), xc[t], acc);
+            if constexpr (MODE == kSplit) {
+                if (c[t] != row && !df64::is_zero(a[t])) {
+                    float ah, al, ph, pl;
+                    df64::split_value(a[t], ah, al);
+                    df64::mul(ah, al, xrh, xrl, ph, pl);
+                    atomicAdd(b + c[t], df64::join(ph, pl));
+                }
+            } else if constexpr (MODE == kFp64) {
+                if (c[t] != row) atomicAdd(b + c[t], static_cast<double>(a[t]) * xr);
+            }
+        }
+    }
+    return acc;
+}
+
+// G lanes per row, rows strided over the grid; the lanes' FP64 row sums are
+// combined by shuffles and go to b[row] as a reduction at L2 (b is zeroed
+// first; transposed updates of other rows land there too).
+template <typename VT, int G>
+__global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                     const double* __restrict__ x, double* b) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = lane_mask<G>();
+    const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
+    for (int64_t r = gid; r < n; r += ngroups) {
+        const int32_t row = static_cast<int32_t>(r);
+        const int32_t lo = __ldg(rp + row), hi = __ldg(rp + row + 1);
+        const double xr = __ldg(x + row);
+        float xrh, xrl;
+        const int st = df64::split(xr, xrh, xrl);
+        double acc;
+        if (st != 0) acc = lane_row<VT, G, kFp64>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        else if (xrh == 0.0f) acc = lane_row<VT, G, kNone>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        else acc = lane_row<VT, G, kSplit>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
+        if (lane == 0) atomicAdd(b + row, acc);
+    }
+}
+
+int sm_count_of_device() {
+    static int count = 0;
+    if (count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+        if (count <= 0) count = 1;
+    }
+    return count;
+}
+
+template <typename VT, int G>
+void launch_g(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    const int64_t threads = static_cast<int64_t>(s->plan.n) * G;
+    const int64_t per_sm = s->launch.blocks_per_sm > 0 ? s->launch.blocks_per_sm : (2048 / kBlock);
+    const int64_t cap = static_cast<int64_t>(sm_count_of_device()) * per_sm;
+    const int blocks = static_cast<int>(std::max<int64_t>(1, std::min((threads + kBlock - 1) / kBlock, cap)));
+    k_symm_df64<VT, G><<<blocks, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, static_cast<const VT*>(s->d_val),
+                                                  x, b);
+}
+
+template <typename VT>
+void launch_vt(const race_schedule* s, int G, const double* x, double* b, cudaStream_t st) {
+    switch (G) {
+        case 1: launch_g<VT, 1>(s, x, b, st); break;
+        case 2: launch_g<VT, 2>(s, x, b, st); break;
+        case 4: launch_g<VT, 4>(s, x, b, st); break;
+        case 8: launch_g<VT, 8>(s, x, b, st); break;
+        case 16: launch_g<VT, 16>(s, x, b, st); break;
+        default: launch_g<VT, 32>(s, x, b, st); break;
+    }
+}
+
+}  // namespace
+
+int race_df64_prepare(const race_schedule* s) {
+    if (s->df64_state == 1) return RACE_OK;
+    if (s->df64_state == -1) {
+        race_set_detail("an off-diagonal value outside the double-float magnitude range [2^-50, 2^51)");
+        return RACE_ERR_UNSUPPORTED;
+    }
+    const int32_t n = s->plan.n;
+    int32_t* d_bad = nullptr;
+    cudaError_t e = cudaMalloc(&d_bad, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int32_t));
+    const int grid = sm_count_of_device() * 8;
+    if (e == cudaSuccess && n > 0) {
+        if (s->val_type == RACE_F64)
+            k_check_offdiag<double><<<grid, kBlock>>>(n, s->d_rp, s->d_col, static_cast<const double*>(s->d_val), d_bad);
+        else
+            k_check_offdiag<float><<<grid, kBlock>>>(n, s->d_rp, s->d_col, static_cast<const float*>(s->d_val), d_bad);
+        e = cudaGetLastError();
+    }
+    int32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (d_bad) cudaFree(d_bad);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("double-float range check: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    s->df64_state = bad ? -1 : 1;
+    if (bad) {
+        race_set_detail("an off-diagonal value outside the double-float magnitude range [2^-50, 2^51)");
+        return RACE_ERR_UNSUPPORTED;
+    }
+    return RACE_OK;
+}
+
+int race_df64_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    int rc = race_df64_prepare(s);
+    if (rc) return rc;
+    const int G = s->launch.executor == RACE_EXEC_DF64_RED ? s->launch.group_lanes : 1;
+    if (s->val_type == RACE_F64) launch_vt<double>(s, G, x, b, st);
+    else launch_vt<float>(s, G, x, b, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("k_symm_df64: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    return RACE_OK;
+}

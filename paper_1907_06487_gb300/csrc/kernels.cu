@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "df64.cuh"
 #include "race_internal.h"
 
 namespace {
@@ -403,7 +404,11 @@ __global__ void __launch_bounds__(kBlock) k_rows_pipe(int32_t n, const int32_t* 
 // group of K lanes owns a row, lane c serves column c, so the K values of
 // a row of X or B are contiguous across the group.  Updates of B are
 // reductions at L2 (B zeroed before).  R rows per group in flight.
-template <typename VT, int K, int R>
+// DF: the transposed updates a_ij X[i][c] in double-float arithmetic on the
+// FP32 and integer pipes (df64.cuh; off-diagonal values range-checked once),
+// the row sums stay FP64; a row whose X[i][c] lies outside the split's range
+// scatters that column in FP64 after its main loop.
+template <typename VT, int K, int R, bool DF>
 __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const int32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
                                                             const VT* __restrict__ val, const double* __restrict__ X,
@@ -414,6 +419,8 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
     for (int64_t r0 = grp; r0 < n; r0 += ngrp * R) {
         int32_t js[R], je[R];
         double xr[R], acc[R];
+        float xrh[R], xrl[R];
+        bool xr64[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int64_t r = r0 + q * ngrp;
@@ -422,17 +429,20 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
             je[q] = v ? __ldg(rp + r + 1) : 0;
             xr[q] = v ? __ldg(X + r * K + c) : 0.0;
             acc[q] = 0.0;
+            xr64[q] = DF && df64::split(xr[q], xrh[q], xrl[q]) != 0;
         }
         int32_t len = 0;
 #pragma unroll
         for (int q = 0; q < R; ++q) len = max(len, je[q] - js[q]);
         for (int32_t p = 0; p < len; ++p) {
+            VT araw[R];
             double a[R], xc[R];
             int32_t cc[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const bool v = js[q] + p < je[q];
-                a[q] = v ? ldv(val + js[q] + p) : 0.0;
+                araw[q] = v ? __ldg(val + js[q] + p) : VT(0);
+                a[q] = static_cast<double>(araw[q]);
                 cc[q] = v ? __ldg(col + js[q] + p) : -1;
             }
 #pragma unroll
@@ -441,7 +451,24 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
             for (int q = 0; q < R; ++q) {
                 if (cc[q] < 0) continue;
                 acc[q] += a[q] * xc[q];
-                if (p > 0) atomicAdd(B + static_cast<int64_t>(cc[q]) * K + c, a[q] * xr[q]);
+                if constexpr (DF) {
+                    if (p > 0 && xrh[q] != 0.0f && !df64::is_zero(araw[q])) {
+                        float ah, al, ph, pl;
+                        df64::split_value(araw[q], ah, al);
+                        df64::mul(ah, al, xrh[q], xrl[q], ph, pl);
+                        atomicAdd(B + static_cast<int64_t>(cc[q]) * K + c, df64::join(ph, pl));
+                    }
+                } else {
+                    if (p > 0) atomicAdd(B + static_cast<int64_t>(cc[q]) * K + c, a[q] * xr[q]);
+                }
+            }
+        }
+        if constexpr (DF) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (!xr64[q]) continue;
+                for (int32_t j = js[q] + 1; j < je[q]; ++j)
+                    atomicAdd(B + static_cast<int64_t>(__ldg(col + j)) * K + c, ldv(val + j) * xr[q]);
             }
         }
 #pragma unroll
@@ -627,12 +654,22 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
         const int32_t n = s->plan.n;
         const int R = s->launch.rows_per_group >= 4 ? 4 : (s->launch.rows_per_group >= 2 ? 2 : 1);
         const VT* v = static_cast<const VT*>(s->d_val);
-#define RACE_MM_ROWS(KK)                                                                                       \
-    do {                                                                                                       \
-        const int g = grid_for((static_cast<int64_t>(n) * KK + R - 1) / R, s->launch.blocks_per_sm);          \
-        if (R == 4) k_symm_mm_rows_red<VT, KK, 4><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);        \
-        else if (R == 2) k_symm_mm_rows_red<VT, KK, 2><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);   \
-        else k_symm_mm_rows_red<VT, KK, 1><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);               \
+        const bool df = s->launch.executor == RACE_EXEC_DF64_RED || s->launch.executor == RACE_EXEC_SELL_DF64;
+        if (df) {
+            const int rc = race_df64_prepare(s);
+            if (rc) return rc;
+        }
+#define RACE_MM_ROWS_DF(KK, DFV)                                                                                   \
+    do {                                                                                                           \
+        const int g = grid_for((static_cast<int64_t>(n) * KK + R - 1) / R, s->launch.blocks_per_sm);              \
+        if (R == 4) k_symm_mm_rows_red<VT, KK, 4, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);        \
+        else if (R == 2) k_symm_mm_rows_red<VT, KK, 2, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);   \
+        else k_symm_mm_rows_red<VT, KK, 1, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);               \
+    } while (0)
+#define RACE_MM_ROWS(KK)                 \
+    do {                                 \
+        if (df) RACE_MM_ROWS_DF(KK, true);  \
+        else RACE_MM_ROWS_DF(KK, false);    \
     } while (0)
         switch (k) {
             case 1: RACE_MM_ROWS(1); break;
@@ -643,6 +680,7 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
             default: return RACE_ERR_UNSUPPORTED;
         }
 #undef RACE_MM_ROWS
+#undef RACE_MM_ROWS_DF
         return RACE_OK;
     }
     switch (k) {
@@ -702,6 +740,8 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
         race_set_detail(std::string("memset: ") + cudaGetErrorString(e));
         return RACE_ERR_CUDA;
     }
+    if (s->launch.executor == RACE_EXEC_DF64_RED) return race_df64_launch(s, x_d, b_d, st);
+    if (s->launch.executor == RACE_EXEC_SELL_DF64) return race_sell_launch(s, x_d, b_d, st);
     if (s->val_type == RACE_F64) launch_symm_exec<double>(s, s->launch.executor, x_d, b_d, st);
     else launch_symm_exec<float>(s, s->launch.executor, x_d, b_d, st);
     return check_launch("symm_spmv");
@@ -710,7 +750,7 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_WINDOW_RACE) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_SELL_DF64) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -720,6 +760,8 @@ int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, 
         race_set_detail(std::string("memset: ") + cudaGetErrorString(e));
         return RACE_ERR_CUDA;
     }
+    if (executor == RACE_EXEC_DF64_RED) return race_df64_launch(s, x_d, b_d, st);
+    if (executor == RACE_EXEC_SELL_DF64) return race_sell_launch(s, x_d, b_d, st);
     if (s->val_type == RACE_F64) launch_symm_exec<double>(s, executor, x_d, b_d, st);
     else launch_symm_exec<float>(s, executor, x_d, b_d, st);
     return check_launch("symm_spmv_exec");
@@ -775,10 +817,18 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool g_ok = l->group_lanes == 1 || l->group_lanes == 2 || l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
-        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_WINDOW_RACE || l->regs_per_row < 0 ||
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_SELL_DF64 || l->regs_per_row < 0 ||
         l->regs_per_row > 16 || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
+    }
+    if (which == 0 && (l->executor == RACE_EXEC_DF64_RED || l->executor == RACE_EXEC_SELL_DF64)) {
+        if (s->host_only) {
+            race_set_detail("schedule was built with RACE_FLAG_HOST_ONLY");
+            return RACE_ERR_UNSUPPORTED;
+        }
+        const int rc = l->executor == RACE_EXEC_DF64_RED ? race_df64_prepare(s) : race_sell_prepare(s);
+        if (rc) return rc;
     }
     if (which == 0) {
         s->launch = *l;

@@ -32,6 +32,8 @@ void release_device(race_schedule* s) {
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
+    s->df64_state = 0;
+    race_free_sell(s->sell);
     for (WindowSet* w : {&s->win_red, &s->win_race}) {
         void* wp[] = {w->d_hdr, w->d_ext, w->d_val, w->d_lidx, w->d_pos, w->d_slot_row, w->d_rs_pos,
                       w->d_chunk_off, w->d_seg, w->d_unit_tile};

@@ -81,6 +81,28 @@ struct WindowSet {
     bool ready = false;
 };
 
+// SELL-32-sigma copy of the permuted upper matrix (sell_kernels.cu): chunks
+// of 32 rows stored column by column; entry j of lane l of chunk k at
+// off[k] + 32 j + l; row[32 k + l] is the row of that lane (-1: none);
+// padding entries have column -1 and value 0.
+constexpr int32_t kSellSigma = 1024;  // rows sorted by length within windows of this size
+
+struct SellHost {
+    std::vector<int64_t> off;
+    std::vector<int32_t> row, col;
+    std::vector<double> val64;
+    std::vector<float> val32;
+};
+
+struct SellSet {
+    int64_t n_chunks = 0, n_stored = 0;
+    int64_t* d_off = nullptr;
+    int32_t* d_row = nullptr;
+    int32_t* d_col = nullptr;
+    void* d_val = nullptr;
+    bool ready = false;
+};
+
 // The opaque handle of the C ABI.
 struct race_schedule {
     race::Plan plan;
@@ -113,6 +135,10 @@ struct race_schedule {
     int32_t* d_status = nullptr;  // device status word (RACE_ERR_TIMEOUT)
     int32_t max_row_upper = 0, max_row_full = 0;
     WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
+    // double-float executor: off-diagonal values range-checked on first use
+    // (0 = not checked, 1 = ready, -1 = a value out of range)
+    mutable int32_t df64_state = 0;
+    mutable SellSet sell;  // built on first use of RACE_EXEC_SELL_DF64
     race_launch launch{};       // symm_spmv executor and shape
     race_launch full_launch{};  // spmv_full shape
 };
@@ -131,6 +157,19 @@ void race_make_tiles(const int32_t* rp, const int32_t* col, const double* val, i
                      WindowHost& out, std::vector<int32_t>& mark, int32_t& stamp);
 int race_window_launch(const race_schedule* s, bool race_mode, const double* x, double* b, cudaStream_t st,
                        int sm_count);
+
+// Double-float executor (df64_kernels.cu): preparation (range check of the
+// off-diagonal values) and the launch, which prepares on first use.
+int race_df64_prepare(const race_schedule* s);
+int race_df64_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
+
+// SELL executor (sell_kernels.cu): layout construction, upload on first use,
+// release, launch.
+void race_make_sell(int32_t n, const int32_t* rp, const int32_t* col, const double* v64, const float* v32,
+                    int32_t sigma, SellHost& out);
+int race_sell_prepare(const race_schedule* s);
+void race_free_sell(SellSet& q);
+int race_sell_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
 
 // Error detail for race_last_error_detail (thread-local).
 void race_set_detail(const std::string& s);

@@ -63,7 +63,7 @@ MATS = [
 ]
 
 
-@pytest.mark.parametrize("executor", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("executor", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("name,mk,nt,eps,md", MATS, ids=[m[0] for m in MATS])
 def test_symm_spmv_parity(dev, oracle_mod, matgen_mod, name, mk, nt, eps, md, executor):
     m = mk(matgen_mod)
@@ -178,12 +178,20 @@ def test_full_size_xxz26(dev, oracle_mod):
     sp, lo, hi = s.phases()
     rows = sample_rows(n, perm[np.concatenate([lo, hi - 1])][:2000], 3000, 1)
     bref, sc = oracle_mod.spmv_sampled(m, x, rows)
+    # the launch the benchmark times (through the default entry point), then
+    # the leaf executors
+    lc = cfg["launch"]
+    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
+                      lc["regs_per_row"])
+    assert_parity(run_symm(s, m, x, dev)[rows], bref, sc)
     for ex in (cfg["executor"], 0):
         b = run_symm(s, m, x, dev, ex)
         assert_parity(b[rows], bref, sc)
     # property at every row: the uniform vector is an eigenvector, eigenvalue L/4 = 6.5,
-    # and every partial sum is a multiple of 1/4 (exact in FP64)
+    # and every partial sum is a multiple of 1/4 (exact in FP64, and in the
+    # double-float products: 0.5 * 1 splits exactly)
     ones = np.ones(n)
+    assert np.all(run_symm(s, m, ones, dev) == 6.5)
     b1 = run_symm(s, m, ones, dev, cfg["executor"])
     assert np.all(b1 == 6.5)
 
@@ -198,6 +206,9 @@ def st27_schedule():
         cfg = configs.SCHEDULE[name]
         _ST27["m"] = m
         _ST27["s"] = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"])
+        lc = cfg["launch"]  # the launch the benchmark times
+        R.race_set_launch(_ST27["s"], 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"],
+                          lc["blocks_per_sm"], lc["regs_per_row"])
     return _ST27["m"], _ST27["s"]
 
 
