@@ -217,6 +217,17 @@ typedef struct {
 int race_set_launch(race_schedule *s, int32_t which, const race_launch *l);
 int race_get_launch(const race_schedule *s, int32_t which, race_launch *l);
 
+/* race_probe_scatter — diagnostic, computes nothing of SymmSpMV.  Replays,
+ * over the schedule's permuted upper matrix and with the row-parallel
+ * executors' access pattern (one row per thread, four entries per step),
+ * either the transposed update's reductions alone (mode 0: b[j] += 1.0 for
+ * every stored a_ij with j != i; b is not zeroed) or the column stream
+ * alone (mode 1: b[i] = sum of row i's column indices).  Timing both
+ * separates the cost of the reductions at L2, the floor of every executor
+ * that scatters by reductions, from the loads.  b_d: device array of n
+ * doubles.  RACE_ERR_INVALID for another mode.                            */
+int race_probe_scatter(const race_schedule *s, int32_t mode, double *b_d, void *stream);
+
 /* race_poll_status — synchronises `stream`, then returns RACE_ERR_TIMEOUT
  * (and clears it) if a bounded device wait of this schedule's kernels gave
  * up since the last poll, else RACE_OK.                                    */

@@ -42,7 +42,7 @@ PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full",
             "race_prepare_full", "race_permute", "race_unpermute", "race_get_perm", "race_get_matrix",
             "race_get_phases", "race_get_info", "race_export", "race_free", "race_strerror",
-            "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status",
+            "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status", "race_probe_scatter",
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
             "race_mlp_backward", "race_mlp_adam", "race_upload")
@@ -128,6 +128,8 @@ def lib():
     L.race_set_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
     L.race_get_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
     L.race_set_launch.restype = ctypes.c_int
+    L.race_probe_scatter.argtypes = [vp, i32, vp, vp]
+    L.race_probe_scatter.restype = ctypes.c_int
     L.race_poll_status.argtypes = [vp, vp]
     L.race_poll_status.restype = ctypes.c_int
     L.symm_spmv_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, vp, vp, vp, vp]
@@ -301,6 +303,11 @@ def race_get_launch(s: Schedule, which):
     lc = race_launch()
     _check(lib().race_get_launch(s.handle, int(which), ctypes.byref(lc)), "race_get_launch")
     return {f: getattr(lc, f) for f, _ in lc._fields_}
+
+
+def race_probe_scatter(s: Schedule, mode, b, stream=None):
+    """Diagnostic: mode 0 replays the scatter's reductions, mode 1 its column stream."""
+    _check(lib().race_probe_scatter(s.handle, int(mode), _ptr(b), _stream(stream)), "race_probe_scatter")
 
 
 def race_poll_status(s: Schedule, stream=None):

@@ -479,6 +479,35 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
     }
 }
 
+// Diagnostics of race_probe_scatter, shaped like the row-parallel executors
+// (one row per thread, four entries per step): mode 0 replays the transposed
+// update's reductions with a constant value, mode 1 streams the column
+// indices alone.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_probe_scatter(int32_t n, const int32_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col, double* b) {
+    const int64_t T = static_cast<int64_t>(gridDim.x) * kBlock;
+    for (int64_t r = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; r < n; r += T) {
+        const int32_t row = static_cast<int32_t>(r);
+        const int32_t lo = __ldg(rp + row), hi = __ldg(rp + row + 1);
+        int32_t sum = 0;
+        for (int32_t idx = lo; idx < hi; idx += 4) {
+            int32_t c[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) c[t] = idx + t < hi ? __ldg(col + idx + t) : -1;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if constexpr (MODE == 0) {
+                    if (c[t] >= 0 && c[t] != row) atomicAdd(b + c[t], 1.0);
+                } else {
+                    sum += c[t] >= 0 ? c[t] : 0;
+                }
+            }
+        }
+        if constexpr (MODE == 1) b[row] = static_cast<double>(sum);
+    }
+}
+
 __global__ void k_permute(int32_t n, int32_t k, const int32_t* __restrict__ perm, const double* __restrict__ in,
                           double* __restrict__ out, int inverse) {
     const int64_t total = static_cast<int64_t>(n) * k;
@@ -860,6 +889,20 @@ int race_poll_status(race_schedule* s, void* stream) {
         return h;
     }
     return RACE_OK;
+}
+
+int race_probe_scatter(const race_schedule* s, int32_t mode, double* b_d, void* stream) {
+    int rc = precheck(s, s ? s->d_rp : nullptr, b_d);
+    if (rc) return rc;
+    if (mode != 0 && mode != 1) {
+        race_set_detail("mode must be 0 (reductions) or 1 (column stream)");
+        return RACE_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int g = grid_for(s->plan.n, 4);
+    if (mode == 0) k_probe_scatter<0><<<g, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, b_d);
+    else k_probe_scatter<1><<<g, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, b_d);
+    return check_launch("race_probe_scatter");
 }
 
 int race_get_launch(const race_schedule* s, int32_t which, race_launch* l) {

@@ -183,3 +183,24 @@ def test_spmm_double_float_scatter(dev, oracle_mod, matgen_mod, k, rows_in_fligh
     Bh = np.empty_like(X)
     Bh[perm] = Bd.cpu().numpy()
     check(Bh, Bref, S)
+
+
+def test_probe_scatter(dev, matgen_mod):
+    """race_probe_scatter: mode 0 adds 1 per stored off-diagonal entry to its
+    column (the lower degree of every row), mode 1 stores the row's sum of
+    column indices."""
+    m = matgen_mod.xxz(12)
+    s = R.race_build(m, 8)
+    pm = s.matrix()
+    n = pm["n"]
+    rows = np.repeat(np.arange(n), np.diff(pm["row_ptr"]))
+    off = pm["col"] != rows
+    bd = torch.zeros(n, dtype=torch.float64, device=dev)
+    R.race_probe_scatter(s, 0, bd)
+    torch.cuda.synchronize()
+    assert np.array_equal(bd.cpu().numpy(), np.bincount(pm["col"][off], minlength=n).astype(np.float64))
+    R.race_probe_scatter(s, 1, bd)
+    torch.cuda.synchronize()
+    assert np.array_equal(bd.cpu().numpy(), np.bincount(rows, weights=pm["col"], minlength=n))
+    with pytest.raises(R.RaceError):
+        R.race_probe_scatter(s, 2, bd)
