@@ -297,8 +297,9 @@ int race_batch_launch(race_batch *b, void *stream);
 void race_batch_free(race_batch *b);
 
 /* race_autotune — times the candidate launch shapes (executors
- * RACE_EXEC_ROWS_RED and RACE_EXEC_PIPE_RED with their lane, row and
- * register shapes, default and 4 blocks per SM) of symm_spmv (k == 1) or
+ * RACE_EXEC_ROWS_RED, RACE_EXEC_PIPE_RED and, when the matrix's values are
+ * in its range, RACE_EXEC_DF64_RED, with their lane, row and register
+ * shapes, default and 4 blocks per SM) of symm_spmv (k == 1) or
  * symm_spmm (k > 1) on the given buffers: one warm-up and `reps` timed
  * calls each, CUDA events on `stream`.  Keeps the fastest as the
  * schedule's launch shape and returns it in *best (and its time per call

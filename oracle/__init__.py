@@ -37,13 +37,15 @@ DEFAULT_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
 
 def build_lib(force: bool = False) -> str:
-    """Compile race_oracle.c (plain C, -O2, no FP contraction)."""
+    """Compile race_oracle.c (plain C, -O2, no FP contraction; OpenMP for
+    the two multi-threaded baselines when the compiler has it)."""
     src = os.path.join(_HERE, "race_oracle.c")
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, src, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, src, "-lm"]
+        if subprocess.call(base + ["-fopenmp"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -59,6 +61,11 @@ def _get():
     L.orc_spmv_full.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, _f64p, _f64p, _f64p]
     L.orc_spmm_full.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, ctypes.c_int32, _f64p, _f64p, _f64p]
     L.orc_symm_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.orc_symm_spmv_race.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p, _i32p,
+                                     _f64p, _f64p, ctypes.c_int32]
+    L.orc_spmv_full_par.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int32]
+    L.orc_max_threads.restype = ctypes.c_int32
+    L.orc_max_threads.argtypes = []
     L.orc_spmv_sampled.restype = ctypes.c_int
     L.orc_spmv_sampled.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _f64p,
                                    ctypes.c_int32, _i32p, _f64p, _f64p]
@@ -137,6 +144,35 @@ def symm_spmv(m, x):
     b = np.zeros(n)
     _get().orc_symm_spmv(n, _p(rp, _i32p), _p(ci, _i32p), _p(va, _f64p), _p(x, _f64p), _p(b, _f64p))
     return b
+
+
+def symm_spmv_race(pm, sched, x, nthreads=0):
+    """Alg. SymmSpMV under the RACE schedule `sched` (an oracle ``Race``) on
+    CPU threads, phase by phase (the paper's execution model).  `pm` is the
+    upper CRS permuted by sched.perm, x in permuted order.  Independent of
+    the thread count, bit for bit."""
+    n, rp, ci, va = _mat(pm)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = np.zeros(n)
+    _get().orc_symm_spmv_race(n, _p(rp, _i32p), _p(ci, _i32p), _p(va, _f64p), sched.n_phases,
+                              _p(sched.stage_ptr, _i32p), _p(sched.leaf_lo, _i32p), _p(sched.leaf_hi, _i32p),
+                              _p(x, _f64p), _p(b, _f64p), int(nthreads))
+    return b
+
+
+def spmv_full_par(full, x, nthreads=0):
+    """b = A x on a full CRS, rows split over CPU threads."""
+    n = full["n"]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = np.zeros(n)
+    _get().orc_spmv_full_par(n, _p(full["row_ptr"], _i64p), _p(full["col"], _i32p), _p(full["val"], _f64p),
+                             _p(x, _f64p), _p(b, _f64p), int(nthreads))
+    return b
+
+
+def max_threads() -> int:
+    """Threads the oracle's OpenMP loops use by default (1 without OpenMP)."""
+    return int(_get().orc_max_threads())
 
 
 def spmv_sampled(m, X, rows):

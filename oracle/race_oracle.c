@@ -18,6 +18,10 @@
  *   orc_symm_spmv      Alg. "SymmSpMV" executed serially (b zeroed first)
  *   orc_spmv_sampled   b_i and s_i of the plain definition for chosen rows
  *                      only, in one pass over the upper CRS
+ *   orc_symm_spmv_race Alg. "SymmSpMV" under a RACE schedule on CPU threads,
+ *                      the paper's own execution model (OpenMP)
+ *   orc_spmv_full_par  Alg. "SpMV using the CRS format" with its rows split
+ *                      over CPU threads (OpenMP), no s
  *
  * Schedule part (integer + FP64 control arithmetic), Section 4:
  *   level construction (Alg. "Construction of levels", Eq. "level"),
@@ -55,6 +59,11 @@
  *      blue children; red children start at the node's offset, blue ones
  *      after the red block.  Empty leaves are not listed.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#else
+static int omp_get_max_threads(void) { return 1; }
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -142,6 +151,57 @@ void orc_symm_spmv(int32_t n, const int32_t *rp, const int32_t *ci, const double
         b[row] += tmp;
     }
 }
+
+/* Alg. "SymmSpMV" under a RACE schedule, executed the way the paper runs it
+ * on a multicore CPU (Sec. 4 and 6): the phases one after another with a
+ * barrier between them; inside a phase the leaves run concurrently, one
+ * leaf per thread at a time, each leaf's rows in order with plain updates
+ * of b.  The leaves of a phase are distance-2 independent, so no two of them
+ * touch one entry of b, and the result does not depend on the thread count
+ * or the interleaving: every b entry receives its updates in phase order,
+ * then row order.  Input: the permuted upper CRS and the flattened phases
+ * (stage_ptr over leaf ranges [lo, hi)).  b is zeroed first.  nthreads <= 0
+ * takes the OpenMP default; without OpenMP the loop runs serially.        */
+void orc_symm_spmv_race(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                        int32_t nphases, const int32_t *stage_ptr, const int32_t *lo, const int32_t *hi,
+                        const double *x, double *b, int32_t nthreads) {
+    (void)nthreads;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    {
+#pragma omp for schedule(static)
+        for (int32_t i = 0; i < n; ++i) b[i] = 0.0;
+        for (int32_t p = 0; p < nphases; ++p) {
+#pragma omp for schedule(dynamic, 1)
+            for (int32_t l = stage_ptr[p]; l < stage_ptr[p + 1]; ++l) {
+                for (int32_t row = lo[l]; row < hi[l]; ++row) {
+                    b[row] += va[rp[row]] * x[row];
+                    double tmp = 0.0;
+                    for (int32_t idx = rp[row] + 1; idx < rp[row + 1]; ++idx) {
+                        tmp += va[idx] * x[ci[idx]];
+                        b[ci[idx]] += va[idx] * x[row];
+                    }
+                    b[row] += tmp;
+                }
+            }
+        }
+    }
+}
+
+/* Alg. "SpMV using the CRS format" with the rows split statically over CPU
+ * threads (OpenMP; serial without it).                                    */
+void orc_spmv_full_par(int32_t n, const int64_t *frp, const int32_t *fci, const double *fva,
+                       const double *x, double *b, int32_t nthreads) {
+    (void)nthreads;
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    for (int32_t row = 0; row < n; ++row) {
+        double tmp = 0.0;
+        for (int64_t idx = frp[row]; idx < frp[row + 1]; ++idx) tmp += fva[idx] * x[fci[idx]];
+        b[row] = tmp;
+    }
+}
+
+/* Threads the OpenMP runtime would use (1 without OpenMP).               */
+int32_t orc_max_threads(void) { return omp_get_max_threads(); }
 
 /* b_i = sum_j a_ij x_j and s_i = sum_j |a_ij||x_j| of the symmetric matrix
  * for the rows listed in rows[0..m), reading the upper CRS once.  Works on

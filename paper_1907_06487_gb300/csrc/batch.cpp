@@ -112,13 +112,19 @@ int race_autotune(race_schedule* s, int32_t k, const double* X_d, double* B_d, i
         return RACE_ERR_UNSUPPORTED;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the double-float executor competes when the matrix's values allow it
+    const bool df = race_df64_prepare(s) == RACE_OK;
     std::vector<race_launch> cand;
     for (int bps : {0, 4}) {
         if (k == 1) {
             for (int g : {1, 2, 4}) cand.push_back({RACE_EXEC_ROWS_RED, g, 1, bps, 8});
             for (int p : {4, 8}) cand.push_back({RACE_EXEC_PIPE_RED, 1, 1, bps, p});
+            if (df)
+                for (int g : {1, 2}) cand.push_back({RACE_EXEC_DF64_RED, g, 1, bps, 4});
         } else {
             for (int r : {1, 2, 4}) cand.push_back({RACE_EXEC_ROWS_RED, 1, r, bps, 8});
+            if (df)
+                for (int r : {1, 2, 4}) cand.push_back({RACE_EXEC_DF64_RED, 1, r, bps, 4});
         }
     }
     const race_launch keep = s->launch;

@@ -1,10 +1,10 @@
 // Double-float ("df64") arithmetic that keeps GB300's FP64 pipe free.
 //
-// On GB300 FP64 multiplies, adds and FP64<->FP32 conversions all issue to a
-// pipe with about 1/70 of the FP32 rate (0.5 T DFMA/s against 35 T FFMA/s),
-// which binds the FP64 SymmSpMV.  These helpers carry a double as an
-// unevaluated sum hi + lo of two floats and do the per-entry work on the FP32
-// and integer pipes:
+// On GB300 FP64 multiplies and adds issue to a pipe with about 1/70 of the
+// FP32 rate (0.5 T DFMA/s against 35 T FFMA/s).  These helpers carry a double
+// as an unevaluated sum hi + lo of two floats and do the per-entry work on
+// the FP32 and integer pipes; the split itself avoids the FP64 subtraction
+// lo = v - hi by reading the bits:
 //   split:  double -> (hi, lo) with integer bit operations and one FP32
 //           subtraction; hi = the leading 24 significant bits, lo = the next
 //           23 bits, so |v - hi - lo| < 2^-46 |v|.  Defined for v = 0 and for

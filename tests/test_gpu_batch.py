@@ -39,7 +39,7 @@ def prepare(mats, k, dev, stream, tune=True):
         Bd = torch.empty_like(Xd)
         if tune:
             launch, us = R.race_autotune(s, k, Xd, Bd, reps=2, stream=stream)
-            assert launch["executor"] in (R.RACE_EXEC_ROWS_RED, R.RACE_EXEC_PIPE_RED) and us > 0
+            assert launch["executor"] in (R.RACE_EXEC_ROWS_RED, R.RACE_EXEC_PIPE_RED, R.RACE_EXEC_DF64_RED) and us > 0
         scheds.append(s); Xs.append(Xd); Bs.append(Bd); Xh.append(X)
     return scheds, Xs, Bs, Xh
 

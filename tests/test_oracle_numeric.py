@@ -162,3 +162,34 @@ def test_xxz26_offdiagonals_match_free_fermion_chain_26(matgen_mod):
     assert n == 10400600
     assert 2 * (len(m["col"]) - n) == 140616112
     assert np.all(m["val"][m["row_ptr"][:-1]] != 0.0)
+
+
+@pytest.mark.parametrize("case", ["xxz14", "st27_14", "geo"])
+def test_race_threaded_symm_spmv(oracle_mod, matgen_mod, case):
+    """The RACE-scheduled multithreaded SymmSpMV (the paper's CPU execution
+    model) equals the plain definition within the parity bound, and -- because
+    a phase's leaves never share an entry of b -- its result is the same bit
+    for bit on 1, 3 and 8 threads."""
+    m = {"xxz14": lambda: matgen_mod.xxz(14), "st27_14": lambda: matgen_mod.stencil3d(14, npt=27, seed=2),
+         "geo": lambda: matgen_mod.geometric(4000, seed=5, mean_degree=8.0)}[case]()
+    sched = oracle_mod.Race(m, 16)
+    pm = oracle_mod.permute_upper(m, sched.perm)
+    x = matgen_mod.uniform(m["n"], 8, -1.0, 1.0)
+    b1 = oracle_mod.symm_spmv_race(pm, sched, x, 1)
+    for t in (3, 8):
+        assert np.array_equal(oracle_mod.symm_spmv_race(pm, sched, x, t), b1)
+    bref, s = oracle_mod.spmv_full(oracle_mod.expand_full(pm), x)
+    assert np.all(np.abs(b1 - bref) <= 1e-12 * s + 1e-300)
+    # one thread, leaves in schedule order = the serial algorithm on the
+    # permuted matrix up to the order of each row's additions
+    assert np.allclose(b1, oracle_mod.symm_spmv(pm, x), rtol=0, atol=1e-12 * float(s.max()))
+
+
+def test_threaded_full_spmv(oracle_mod, matgen_mod):
+    m = matgen_mod.anderson(12, W=4.0, seed=3)
+    full = oracle_mod.expand_full(m)
+    x = matgen_mod.uniform(m["n"], 4, -1.0, 1.0)
+    b, _ = oracle_mod.spmv_full(full, x)
+    for t in (1, 4):
+        assert np.array_equal(oracle_mod.spmv_full_par(full, x, t), b)
+    assert oracle_mod.max_threads() >= 1
