@@ -50,6 +50,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(times, world, device):
+    """Element-wise max of the per-rank timings (seconds) over all ranks; a
+    no-op for one rank.  `device` is where the collective runs (cuda for
+    NCCL, cpu for gloo)."""
+    import torch
+    t = torch.tensor([float(v) for v in times], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(world, units_per_step, steps, seconds):
+    """Whole-job throughput: every rank processes `units_per_step` per step
+    (replicas, weak scaling), timed by the slowest rank."""
+    return world * units_per_step * steps / seconds
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -59,10 +76,12 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(files=None):
+    """Hash of the kernel sources: the listed files of csrc/ (those that
+    define the profiled kernel), or all of them."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1907_06487_gb300", "csrc")
-    for name in sorted(os.listdir(cs)):
+    for name in sorted(files if files else os.listdir(cs)):
         with open(os.path.join(cs, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -77,7 +96,7 @@ def ncu_traffic(workload, kernel):
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("sources") != kernel_sources_hash():
+    if not e or e.get("sources") != kernel_sources_hash(e.get("source_files")):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -282,6 +301,24 @@ def run_ours(args):
     t_red, t_col = probe(0), probe(1)
     # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
     t_full = timed(lambda i: R.spmv_full(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    # ---- the conflict-free RACE executors on the same schedule (a few steps: they are slow),
+    # 8 lanes per row in the leaf executor, then the benchmark's launch again
+    R.race_set_launch(s, 0, R.RACE_EXEC_LEAF_CTA, 8, 1, 0, 8)
+    t_leaf_cta = timed(lambda i: R.symm_spmv(s, xs[i % ring], bs[i % ring], stream), 3, 1)
+    t_win_race = timed(lambda i: R.symm_spmv_exec(s, R.RACE_EXEC_WINDOW_RACE, xs[i % ring], bs[i % ring], stream),
+                       3, 1)
+    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
+                      lc["regs_per_row"])
+    # ---- the same two kernels on the input order (no RACE permutation) --------------------
+    s_nat = R.race_build(m, cfg["n_workers"], natural_order=True, windows=False, stream=stream)
+    R.race_set_launch(s_nat, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
+                      lc["regs_per_row"])
+    R.race_prepare_full(s_nat, stream)
+    R.race_set_launch(s_nat, 1, fl["executor"], fl["group_lanes"], fl["rows_per_group"], fl["blocks_per_sm"],
+                      fl["regs_per_row"])
+    t_nat_symm = timed(lambda i: R.symm_spmv(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    t_nat_full = timed(lambda i: R.spmv_full(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    s_nat.free()
     # ---- end to end through host buffers: H2D x, permute, SymmSpMV, unpermute, D2H b --------
     # Each step copies its x in and its b out; copies run on their own streams
     # (double-buffered), so step i's read-back overlaps step i+1's upload and
@@ -337,17 +374,13 @@ def run_ours(args):
     ref = bd[0].cpu().numpy()
     got = bh[(args.steps - 1) % 2].numpy()
     e2e_ok = bool(np.allclose(got, ref, rtol=1e-12, atol=1e-12 * float(np.abs(ref).max())))
-    # max over ranks
-    times = torch.tensor([t_symm, t_full, t_e2e, t_red, t_col], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t_symm, t_full, t_e2e, t_red, t_col = (float(v) for v in times.cpu())
+    t_symm, t_full, t_e2e, t_red, t_col = max_over_ranks([t_symm, t_full, t_e2e, t_red, t_col], world, dev)
 
     flops = pm.flops(nf)
     per_step = t_symm / args.steps
-    value = world * flops * args.steps / t_symm / 1e9
-    full_gflops = world * flops * args.steps / t_full / 1e9
-    e2e_value = world * flops * args.steps / t_e2e / 1e9
+    value = whole_job_rate(world, flops, args.steps, t_symm) / 1e9
+    full_gflops = whole_job_rate(world, flops, args.steps, t_full) / 1e9
+    e2e_value = whole_job_rate(world, flops, args.steps, t_e2e) / 1e9
     sym_bytes = pm.symm_bytes(n, nu)
     achieved = sym_bytes / per_step / 1e9
     peak, peak_kind = load_peaks()
@@ -381,6 +414,16 @@ def run_ours(args):
                                     "executors' access pattern; frac = that floor / SymmSpMV time"},
         "spmv_full": {"value": full_gflops, "unit": "GFLOP/s", "ms_per_step": t_full / args.steps * 1e3,
                       "gbs": pm.full_bytes(n, nf) / (t_full / args.steps) / 1e9},
+        "natural_order": {"symm_ms_per_step": t_nat_symm / args.steps * 1e3,
+                          "symm_gflops": flops / (t_nat_symm / args.steps) / 1e9,
+                          "full_ms_per_step": t_nat_full / args.steps * 1e3,
+                          "speedup_vs_full": t_nat_full / t_nat_symm,
+                          "what": "the same launches on the input order (RACE_FLAG_NATURAL_ORDER: no permutation)"},
+        "race_conflict_free": {"leaf_cta_ms_per_step": t_leaf_cta / 3 * 1e3,
+                               "window_race_ms_per_step": t_win_race / 3 * 1e3,
+                               "n_workers": cfg["n_workers"], "n_phases": info["n_phases"],
+                               "what": "RACE_EXEC_LEAF_CTA and RACE_EXEC_WINDOW_RACE (phase by phase, no two concurrent "
+                                       "leaves share an entry of b) on the benchmark schedule, 3 steps each"},
         "speedup_vs_full": t_full / t_symm,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
@@ -462,23 +505,60 @@ def run_batch(args):
     time.sleep(0.3)
     t = timed(lambda i: batch.launch(stream), args.steps, args.warmup)
     clk = clocks.stop()
-    # end to end: H2D of every X from pinned host memory, graph, D2H of every B
+    # end to end: H2D of every X from pinned host memory, graph, D2H of every B.  Two buffer
+    # sets with a graph each, alternating, copies on their own streams: step i's read-back
+    # overlaps step i+1's upload and replay.
     xh = [torch.from_numpy(np.ascontiguousarray(X[s.perm()])).pin_memory() for X, s in zip(Xh, scheds)]
-    bh = [torch.empty_like(h).pin_memory() for h in xh]
+    bh = [[torch.empty_like(h).pin_memory() for h in xh] for _ in range(2)]
+    X2 = [Xs, [torch.empty_like(x) for x in Xs]]
+    B2 = [Bs, [torch.empty_like(b) for b in Bs]]
+    batches = [batch, R.race_batch_create(scheds, k, X2[1], B2[1], stream)]
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
 
-    def e2e(_):
-        for h, d in zip(xh, Xs):
-            d.copy_(h, non_blocking=True)
-        batch.launch(stream)
-        for h, d in zip(bh, Bs):
-            h.copy_(d, non_blocking=True)
+    def e2e(i):
+        j = i % 2
+        s_in.wait_event(ev_c[j])
+        with torch.cuda.stream(s_in):
+            for h, d in zip(xh, X2[j]):
+                d.copy_(h, non_blocking=True)
+        ev_in[j].record(s_in)
+        stream.wait_event(ev_in[j])
+        stream.wait_event(ev_out[j])
+        batches[j].launch(stream)
+        ev_c[j].record(stream)
+        s_out.wait_event(ev_c[j])
+        with torch.cuda.stream(s_out):
+            for h, d in zip(bh[j], B2[j]):
+                h.copy_(d, non_blocking=True)
+        ev_out[j].record(s_out)
 
-    with torch.cuda.stream(stream):
-        t_e2e = timed(e2e, args.steps, args.warmup)
-    times = torch.tensor([t, t_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t, t_e2e = (float(v) for v in times.cpu())
+    def timed_e2e(steps, warmup):
+        for i in range(warmup):
+            e2e(i)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        for i in range(steps):
+            e2e(i)
+        stream.wait_stream(s_out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        return e0.elapsed_time(e1) * 1e-3
+
+    t_e2e = timed_e2e(args.steps, args.warmup)
+    # the read-back of the last step equals the graph's result on the same X
+    last = (args.steps - 1) % 2
+    e2e_ok = all(bool(np.allclose(h.numpy(), d.cpu().numpy(), rtol=1e-12, atol=1e-300))
+                 for h, d in zip(bh[last], B2[last]))
+    batches[1].free()
+    t, t_e2e = max_over_ranks([t, t_e2e], world, dev)
     per = t / args.steps
     achieved = sym_bytes / per / 1e9
     peak, peak_kind = load_peaks()
@@ -486,7 +566,7 @@ def run_batch(args):
         nbytes = sum(x.numel() * 8 for x in xh)
         print(json.dumps({
             "metric": "SymmSpMM GFLOP/s (2*nnz_full*k flops) of a 64-matrix batch in one CUDA graph",
-            "value": world * flops * args.steps / t / 1e9, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "value": whole_job_rate(world, flops, args.steps, t) / 1e9, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch64", "k": k, "matrices": len(mats),
@@ -494,15 +574,18 @@ def run_batch(args):
                        "l2": "inputs larger than L2 (all matrices and blocks: several GB per replay)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_step": sym_bytes},
-            "e2e": {"value": world * flops * args.steps / t_e2e / 1e9, "unit": "GFLOP/s",
-                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "e2e": {"value": whole_job_rate(world, flops, args.steps, t_e2e) / 1e9, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
+                    "how": "per step: pinned H2D of every X, one graph replay, D2H of every B; two buffer sets "
+                           "and graphs alternate, copies on their own streams"},
             "gpu_launches": len(mats) * args.steps, "clocks": clk, "cpu_baseline": None,
             "setup_seconds": setup_s}))
     batch.free()
     return 0
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -512,7 +595,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":

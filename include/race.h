@@ -61,6 +61,11 @@ extern "C" {
                                    tiles (faster builds; the window
                                    executors then fall back to
                                    RACE_EXEC_ROWS_RED)                      */
+#define RACE_FLAG_NATURAL_ORDER 4u /* no RACE schedule: identity permutation
+                                   and one phase whose single leaf holds every
+                                   row.  For comparisons on the input order
+                                   (the row-parallel executors run as usual;
+                                   the leaf executors then run serially).   */
 
 /* Upper-triangle CRS matrix in HOST memory (Sec. 3.2, Alg. "SymmSpMV"):
  * row i holds the entries (i, j) with j >= i.  Columns may come in any

@@ -35,6 +35,7 @@ RACE_BAL_ROWS = 0
 RACE_BAL_NNZ = 1
 RACE_FLAG_HOST_ONLY = 1
 RACE_FLAG_NO_WINDOWS = 2
+RACE_FLAG_NATURAL_ORDER = 4
 
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
@@ -201,7 +202,7 @@ def _check(rc, where):
 
 
 def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False,
-                windows=True):
+                windows=True, natural_order=False):
     p = race_params()
     lib().race_default_params(ctypes.byref(p), int(n_workers))
     e = list(eps) + [eps[-1]] * (8 - len(eps))
@@ -210,7 +211,8 @@ def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, g
     p.max_depth = int(max_depth)
     p.balance = int(balance)
     p.group_lanes = int(group_lanes)
-    p.flags = (RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
+    p.flags = ((RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
+               | (RACE_FLAG_NATURAL_ORDER if natural_order else 0))
     return p
 
 
@@ -274,7 +276,7 @@ class Schedule:
 
 
 def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
-               host_only=False, stream=None, val_type=RACE_F64, windows=True) -> Schedule:
+               host_only=False, stream=None, val_type=RACE_F64, windows=True, natural_order=False) -> Schedule:
     """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
     n = int(m["n"])
     rp = np.ascontiguousarray(m["row_ptr"], dtype=np.int32)
@@ -282,7 +284,7 @@ def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS,
     val = np.ascontiguousarray(m["val"], dtype=np.float64 if val_type == RACE_F64 else np.float32)
     a = race_csr_upper(n, int(rp[-1]) if n > 0 else 0, rp.ctypes.data, col.ctypes.data if len(col) else None,
                        val.ctypes.data if len(val) else None, int(val_type))
-    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows)
+    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows, natural_order)
     h = ctypes.c_void_p()
     _check(lib().race_build(ctypes.byref(a), ctypes.byref(p), _stream(stream), ctypes.byref(h)), "race_build")
     return Schedule(h.value, n)

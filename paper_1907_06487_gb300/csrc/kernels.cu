@@ -434,34 +434,46 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
         int32_t len = 0;
 #pragma unroll
         for (int q = 0; q < R; ++q) len = max(len, je[q] - js[q]);
-        for (int32_t p = 0; p < len; ++p) {
-            VT araw[R];
-            double a[R], xc[R];
-            int32_t cc[R];
+        // U entries of each of the R rows per step: all loads of a step are
+        // issued before their uses (two dependent round trips per step, not
+        // per entry)
+        constexpr int U = 4;
+        for (int32_t p = 0; p < len; p += U) {
+            VT araw[R][U];
+            double xc[R][U];
+            int32_t cc[R][U];
 #pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const bool v = js[q] + p < je[q];
-                araw[q] = v ? __ldg(val + js[q] + p) : VT(0);
-                a[q] = static_cast<double>(araw[q]);
-                cc[q] = v ? __ldg(col + js[q] + p) : -1;
-            }
+            for (int q = 0; q < R; ++q)
 #pragma unroll
-            for (int q = 0; q < R; ++q) xc[q] = cc[q] >= 0 ? __ldg(X + static_cast<int64_t>(cc[q]) * K + c) : 0.0;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                if (cc[q] < 0) continue;
-                acc[q] += a[q] * xc[q];
-                if constexpr (DF) {
-                    if (p > 0 && xrh[q] != 0.0f && !df64::is_zero(araw[q])) {
-                        float ah, al, ph, pl;
-                        df64::split_value(araw[q], ah, al);
-                        df64::mul(ah, al, xrh[q], xrl[q], ph, pl);
-                        atomicAdd(B + static_cast<int64_t>(cc[q]) * K + c, df64::join(ph, pl));
-                    }
-                } else {
-                    if (p > 0) atomicAdd(B + static_cast<int64_t>(cc[q]) * K + c, a[q] * xr[q]);
+                for (int u = 0; u < U; ++u) {
+                    const bool v = js[q] + p + u < je[q];
+                    araw[q][u] = v ? __ldg(val + js[q] + p + u) : VT(0);
+                    cc[q][u] = v ? __ldg(col + js[q] + p + u) : -1;
                 }
-            }
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    xc[q][u] = cc[q][u] >= 0 ? __ldg(X + static_cast<int64_t>(cc[q][u]) * K + c) : 0.0;
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (cc[q][u] < 0) continue;
+                    const double a = static_cast<double>(araw[q][u]);
+                    acc[q] = fma(a, xc[q][u], acc[q]);
+                    if (p + u == 0) continue;  // the diagonal (first entry) has no transposed update
+                    if constexpr (DF) {
+                        if (xrh[q] != 0.0f && !df64::is_zero(araw[q][u])) {
+                            float ah, al, ph, pl;
+                            df64::split_value(araw[q][u], ah, al);
+                            df64::mul(ah, al, xrh[q], xrl[q], ph, pl);
+                            atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, df64::join(ph, pl));
+                        }
+                    } else {
+                        atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, a * xr[q]);
+                    }
+                }
         }
         if constexpr (DF) {
 #pragma unroll

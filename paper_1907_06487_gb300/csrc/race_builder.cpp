@@ -451,6 +451,33 @@ void build_plan(int32_t n, const int32_t* row_ptr, const int32_t* col, const rac
     b.run();
 }
 
+void natural_plan(int32_t n, const race_params& p, Plan& out) {
+    out = Plan();
+    out.n = n;
+    out.n_workers = p.n_workers;
+    out.dist_k = p.dist_k;
+    out.balance = p.balance;
+    out.max_depth = 0;
+    for (int i = 0; i < 8; ++i) out.eps[i] = p.eps[i];
+    out.perm.resize(static_cast<size_t>(n));
+    for (int32_t i = 0; i < n; ++i) out.perm[static_cast<size_t>(i)] = i;
+    TreeNode root;
+    root.lo = 0;
+    root.hi = n;
+    root.n_threads = 1;
+    root.size = n;
+    root.neff = n;
+    out.nodes.push_back(root);
+    out.stage_ptr = {0};
+    if (n > 0) {
+        out.stage_ptr.push_back(1);
+        out.leaf_lo = {0};
+        out.leaf_hi = {n};
+    }
+    // one leaf holds every row: N_eff = n, eta = n / (N_eff * N_t)
+    out.eta = p.n_workers > 0 ? 1.0 / p.n_workers : 1.0;
+}
+
 std::vector<uint8_t> export_plan(const Plan& plan) {
     std::vector<uint8_t> o;
     const int32_t phases = static_cast<int32_t>(plan.stage_ptr.size()) - 1;

@@ -306,7 +306,8 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
             delete s;
             return rc;
         }
-        race::build_plan(a->n, rp.data(), col.data(), *p, s->plan);
+        if (p->flags & RACE_FLAG_NATURAL_ORDER) race::natural_plan(a->n, *p, s->plan);
+        else race::build_plan(a->n, rp.data(), col.data(), *p, s->plan);
         permute_upper(a->n, rp, col, val, s->plan.perm, s->h_rp, s->h_col, s->h_val64);
         s->val_type = a->val_type;
         if (a->val_type == RACE_F32) {

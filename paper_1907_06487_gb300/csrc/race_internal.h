@@ -42,6 +42,10 @@ struct Plan {
 // rows are canonical (diagonal first, strictly increasing columns).
 void build_plan(int32_t n, const int32_t* row_ptr, const int32_t* col, const race_params& p, Plan& out);
 
+// The plan of RACE_FLAG_NATURAL_ORDER: identity permutation, one phase
+// holding one leaf with every row.
+void natural_plan(int32_t n, const race_params& p, Plan& out);
+
 // Canonical export image (layout documented in race.h).
 std::vector<uint8_t> export_plan(const Plan& plan);
 

@@ -204,3 +204,14 @@ def test_probe_scatter(dev, matgen_mod):
     assert np.array_equal(bd.cpu().numpy(), np.bincount(rows, weights=pm["col"], minlength=n))
     with pytest.raises(R.RaceError):
         R.race_probe_scatter(s, 2, bd)
+
+
+@pytest.mark.parametrize("exe", [R.RACE_EXEC_LEAF_GROUP, R.RACE_EXEC_ROWS_RED, DF, SELL])
+def test_natural_order(dev, oracle_mod, matgen_mod, exe):
+    """Without a RACE schedule (input order, one leaf) every executor still
+    computes SymmSpMV; the leaf executor then runs the rows serially."""
+    m = matgen_mod.xxz(12)
+    s = R.race_build(m, 16, natural_order=True)
+    x = matgen_mod.uniform(m["n"], 15, -1.0, 1.0)
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
+    check(run(s, x, dev, exe), bref, sc)

@@ -162,3 +162,19 @@ def test_single_row_and_diagonal_only(lib, oracle_mod):
             "val": np.arange(1, n + 1, dtype=np.float64)}
     s = R.race_build(diag, 4, host_only=True)
     assert s.export() == oracle_mod.Race(diag, 4).export()
+
+
+def test_natural_order_plan(matgen_mod):
+    """RACE_FLAG_NATURAL_ORDER: identity permutation, the canonical input
+    matrix unchanged, one phase with one leaf covering every row."""
+    import paper_1907_06487_gb300 as R
+    m = matgen_mod.anderson(6, seed=2)
+    s = R.race_build(m, 8, host_only=True, natural_order=True)
+    inf = s.info()
+    assert inf["n_phases"] == 1 and inf["n_leaves"] == 1
+    assert np.array_equal(s.perm(), np.arange(m["n"]))
+    pm = s.matrix()
+    for key in ("row_ptr", "col", "val"):
+        assert np.array_equal(pm[key], m[key])
+    sp, lo, hi = s.phases()
+    assert list(sp) == [0, 1] and lo[0] == 0 and hi[0] == m["n"]
