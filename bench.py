@@ -50,6 +50,10 @@ def dist_env():
     return rank, world, local
 
 
+# SymmSpMM right-hand-side counts timed per workload (SURVEY config 3: k = 4, 8, 16)
+SPMM_KS = {"st27_200": (4, 8, 16)}
+
+
 def max_over_ranks(times, world, device):
     """Element-wise max of the per-rank timings (seconds) over all ranks; a
     no-op for one rank.  `device` is where the collective runs (cuda for
@@ -193,6 +197,19 @@ def oracle_cpu(m, name, seconds):
     }
 
 
+def oracle_normwise_error(m, x, b_perm, perm):
+    """||b - b_ref||_2 / || |A||x| ||_2 of a result b (given in the schedule's
+    permuted order) against the FP64 oracle's plain definition (part of the
+    CPU-baseline leg: the only place bench.py runs the oracle)."""
+    import numpy as np
+
+    import oracle
+    bref, s = oracle.spmv_full(oracle.expand_full(m), x)
+    b = np.empty_like(bref)
+    b[perm] = b_perm
+    return float(np.linalg.norm(b - bref) / np.linalg.norm(s))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -319,6 +336,29 @@ def run_ours(args):
     t_nat_symm = timed(lambda i: R.symm_spmv(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     t_nat_full = timed(lambda i: R.spmv_full(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     s_nat.free()
+    # ---- FP32-stored values (x, b and the row sums stay FP64), same launch -----------------
+    s32 = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
+                       val_type=R.RACE_F32, windows=False)
+    R.race_set_launch(s32, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
+                      lc["regs_per_row"])
+    t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    # the FP32-valued result for x_host, kept for the normwise error against the FP64 oracle
+    with torch.cuda.stream(stream):
+        R.symm_spmv(s32, xs[0], bs[0], stream)
+    stream.synchronize()
+    b32_perm = bs[0].cpu().numpy()
+    s32.free()
+    # ---- SymmSpMM with several right-hand sides (workloads that name them) ------------------
+    spmm = {}
+    for k in SPMM_KS.get(name, ()):
+        with torch.cuda.stream(stream):
+            Xk = [torch.rand(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+            Bk = [torch.empty(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+        tk = timed(lambda i: R.symm_spmm(s, k, Xk[i % 2], Bk[i % 2], stream), max(3, args.steps // 4), 2)
+        per_k = tk / max(3, args.steps // 4)
+        spmm[str(k)] = {"ms_per_step": per_k * 1e3, "gflops": pm.flops(nf, k) / per_k / 1e9,
+                        "gbs": pm.symm_bytes(n, nu, k) / per_k / 1e9}
+        del Xk, Bk
     # ---- end to end through host buffers: H2D x, permute, SymmSpMV, unpermute, D2H b --------
     # Each step copies its x in and its b out; copies run on their own streams
     # (double-buffered), so step i's read-back overlaps step i+1's upload and
@@ -390,8 +430,10 @@ def run_ours(args):
 
     # CPU baseline: the oracle on a bounded sample (a few serial sweeps)
     cpu = None
+    fp32_err = None
     if not args.no_cpu_baseline:
         cpu = oracle_cpu(m, name, args.cpu_seconds)
+        fp32_err = oracle_normwise_error(m, x_host, b32_perm, perm)
     traffic = ncu_traffic(name, "symm")
     line = {
         "metric": "SymmSpMV GFLOP/s (2*nnz_full flops per step) on 1 GB300 vs full-CRS SpMV",
@@ -414,6 +456,13 @@ def run_ours(args):
                                     "executors' access pattern; frac = that floor / SymmSpMV time"},
         "spmv_full": {"value": full_gflops, "unit": "GFLOP/s", "ms_per_step": t_full / args.steps * 1e3,
                       "gbs": pm.full_bytes(n, nf) / (t_full / args.steps) / 1e9},
+        "fp32_values": {"ms_per_step": t_f32 / args.steps * 1e3, "gflops": flops / (t_f32 / args.steps) / 1e9,
+                        "gbs": pm.symm_bytes(n, nu, 1, 4) / (t_f32 / args.steps) / 1e9,
+                        "normwise_error_vs_fp64_oracle": fp32_err,
+                        "what": "values stored in FP32 (8 B per stored entry), x, b and row sums FP64; error = "
+                                "||b32 - b_ref||_2 / || |A||x| ||_2 against the FP64 oracle (computed in the CPU "
+                                "baseline leg; null without it)"},
+        "spmm": spmm,
         "natural_order": {"symm_ms_per_step": t_nat_symm / args.steps * 1e3,
                           "symm_gflops": flops / (t_nat_symm / args.steps) / 1e9,
                           "full_ms_per_step": t_nat_full / args.steps * 1e3,

@@ -85,6 +85,13 @@ DF_HD double u2d(uint32_t hi, uint32_t lo) {
     return v;
 #endif
 }
+DF_HD int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __clz(static_cast<int>(x));
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
 DF_HD float fmul(float a, float b) {
 #ifdef __CUDA_ARCH__
     return __fmul_rn(a, b);
@@ -145,6 +152,34 @@ DF_HD void split_in_range(double v, float& hi, float& lo) {
     hi = u2f(hb);
     lo = fsub(u2f(base | ((L >> 6) & 0x7FFFFFu)), u2f(base));
 }
+
+// The double equal to a float, built from its bits with integer operations
+// (the widening conversion issues to the FP64 pipe on GB300).  Exact for
+// every float: normal (exponent + 896, mantissa << 29), zero, subnormal
+// (normalised by its leading bit), infinity and NaN (payload kept, quiet bit
+// set, as an IEEE conversion does).
+DF_HD double widen(float v) {
+    const uint32_t u = f2u(v);
+    const uint32_t sign = u & 0x80000000u;
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint32_t m = u & 0x7FFFFFu;
+    uint32_t hi = sign | ((e + 896u) << 20) | (m >> 3);
+    uint32_t lo = m << 29;
+    if (e == 0xFFu) hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);  // NaN comes out quiet
+    if (e == 0) {  // integer work only, so a predicated form costs no FP64 issue
+        if (m == 0) {
+            hi = sign;
+            lo = 0;
+        } else {
+            const int p = 31 - clz32(m);  // leading bit of m * 2^-149
+            const uint32_t f = (m << (23 - p)) & 0x7FFFFFu;
+            hi = sign | (static_cast<uint32_t>(p + 874) << 20) | (f >> 3);
+            lo = f << 29;
+        }
+    }
+    return u2d(hi, lo);
+}
+DF_HD double widen(double v) { return v; }
 
 // Zero test and split of a stored value (double: checked range, see above;
 // float: its own hi part).

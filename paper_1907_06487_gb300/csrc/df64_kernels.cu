@@ -95,7 +95,7 @@ __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, 
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (c[t] < 0) continue;
-            acc = fma(static_cast<double>(a[t]), xc[t], acc);
+            acc = fma(df64::widen(a[t]), xc[t], acc);
             if constexpr (MODE == kSplit) {
                 if (c[t] != row && !df64::is_zero(a[t])) {
                     float ah, al, ph, pl;
@@ -104,7 +104,7 @@ __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, 
                     atomicAdd(b + c[t], df64::join(ph, pl));
                 }
             } else if constexpr (MODE == kFp64) {
-                if (c[t] != row) atomicAdd(b + c[t], static_cast<double>(a[t]) * xr);
+                if (c[t] != row) atomicAdd(b + c[t], df64::widen(a[t]) * xr);
             }
         }
     }

@@ -39,9 +39,11 @@ __device__ __forceinline__ double group_sum(double v, unsigned mask) {
     return v;
 }
 
+// A stored value as a double; FP32 values are widened with integer
+// operations (df64::widen), not on the FP64 pipe.
 template <typename VT>
 __device__ __forceinline__ double ldv(const VT* p) {
-    return static_cast<double>(__ldg(p));
+    return df64::widen(__ldg(p));
 }
 
 // One phase of SymmSpMV: leaves [0, nleaf) of this phase.
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (cc[q][u] < 0) continue;
-                    const double a = static_cast<double>(araw[q][u]);
+                    const double a = df64::widen(araw[q][u]);
                     acc[q] = fma(a, xc[q][u], acc[q]);
                     if (p + u == 0) continue;  // the diagonal (first entry) has no transposed update
                     if constexpr (DF) {

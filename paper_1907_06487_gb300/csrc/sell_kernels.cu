@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_sell(int64_t n_chunks, const in
             for (int t = 0; t < U; ++t) xc[t] = c[t] >= 0 ? __ldg(x + c[t]) : 0.0;
 #pragma unroll
             for (int t = 0; t < U; ++t) {
-                acc = fma(static_cast<double>(a[t]), xc[t], acc);
+                acc = fma(df64::widen(a[t]), xc[t], acc);
                 if (scatter && c[t] >= 0 && c[t] != row && !df64::is_zero(a[t])) {
                     float ah, al, ph, pl;
                     df64::split_value(a[t], ah, al);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_sell(int64_t n_chunks, const in
         if (st != 0) {  // x_row outside the split's range: this row scatters in FP64
             for (int32_t jj = 0; jj < w; ++jj) {
                 const int32_t c = __ldg(cp + static_cast<int64_t>(jj) * kChunk);
-                if (c >= 0 && c != row) atomicAdd(b + c, static_cast<double>(__ldg(vp + static_cast<int64_t>(jj) * kChunk)) * xr);
+                if (c >= 0 && c != row) atomicAdd(b + c, df64::widen(__ldg(vp + static_cast<int64_t>(jj) * kChunk)) * xr);
             }
         }
         if (row >= 0) atomicAdd(b + row, acc);

@@ -2,6 +2,8 @@
 // forms the transposed products on the FP32 and integer pipes, exported for
 // the CPU tests (compiled with contraction off, so every FP32 operation
 // rounds exactly as on the device).
+#include <initializer_list>
+
 #include "../../paper_1907_06487_gb300/csrc/df64.cuh"
 
 extern "C" {
@@ -29,6 +31,27 @@ double df_scatter(double a, double xr) {
     df64::split_in_range(a, ah, al);
     df64::mul(ah, al, xh, xl, ph, pl);
     return df64::join(ph, pl);
+}
+
+// Mismatches of df64::widen against the (double) cast over the floats whose
+// bit patterns run from `start` to `end` in steps of `stride` (plus the
+// special values), compared bit for bit.
+long long df_widen_mismatches(unsigned start, unsigned stride, unsigned end) {
+    long long bad = 0;
+    auto check = [&](uint32_t u) {
+        float f;
+        std::memcpy(&f, &u, 4);
+        const double a = df64::widen(f), b = static_cast<double>(f);
+        uint64_t ua, ub;
+        std::memcpy(&ua, &a, 8);
+        std::memcpy(&ub, &b, 8);
+        if (ua != ub) ++bad;
+    };
+    for (uint64_t u = start; u <= end; u += stride) check(static_cast<uint32_t>(u));
+    for (uint32_t u : {0u, 0x80000000u, 1u, 0x80000001u, 0x7FFFFFu, 0x807FFFFFu, 0x800000u, 0x7F7FFFFFu,
+                       0x7F800000u, 0xFF800000u, 0x7FC00000u, 0x7FA00001u, 0x3F800000u})
+        check(u);
+    return bad;
 }
 
 }  // extern "C"

@@ -39,6 +39,8 @@ def df(tmp_path_factory):
     lib.df_two_sum.argtypes, lib.df_two_sum.restype = [f, f, pf, pf], None
     lib.df_fast_two_sum.argtypes, lib.df_fast_two_sum.restype = [f, f, pf, pf], None
     lib.df_scatter.argtypes, lib.df_scatter.restype = [d, d], d
+    lib.df_widen_mismatches.argtypes = [ctypes.c_uint, ctypes.c_uint, ctypes.c_uint]
+    lib.df_widen_mismatches.restype = ctypes.c_longlong
     return lib
 
 
@@ -182,3 +184,14 @@ def test_scatter_products(df):
     assert df.df_scatter(3.0, 0.0) == 0.0
     assert df.df_scatter(3.0, 2.0 ** 70) == 3.0 * 2.0 ** 70  # x outside the range: FP64
     assert math.isnan(df.df_scatter(3.0, math.nan))
+
+
+def test_widen_is_the_exact_conversion(df):
+    """Integer widening of FP32 values equals the (double) cast bit for bit:
+    floats 65,537 and 65,521 bit patterns apart over the whole 32-bit range
+    (all exponents, both signs, infinities, NaNs), every subnormal of both
+    signs, and the special values."""
+    assert df.df_widen_mismatches(0, 65537, 0xFFFFFFFF) == 0
+    assert df.df_widen_mismatches(12345, 65521, 0xFFFFFFFF) == 0
+    assert df.df_widen_mismatches(0, 1, 0x7FFFFF) == 0
+    assert df.df_widen_mismatches(0x80000000, 1, 0x807FFFFF) == 0
