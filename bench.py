@@ -39,6 +39,7 @@ WORKLOAD_DESC = {
     "st27_200": "3D 27-point stencil 200^3 nonperiodic SPD, off-diag -U(0,1] seed 4, FP64 upper CRS",
     "anderson32": "3D Anderson 32^3 periodic 7-pt, disorder U[-8.25,8.25) seed 1, FP64 upper CRS",
     "xxz24": "Heisenberg XXZ chain L=24 periodic, Sz=0 (2,704,156 rows), FP64 upper CRS (small profiling case)",
+    "st27_100": "3D 27-point stencil 100^3 nonperiodic SPD, FP64 upper CRS (small profiling case of st27_200)",
     "batch64": "64 matrices: Anderson L~U[16,96] and geometric graphs n~U[1e4,1e6] (mean degree 20), FP64, k=4",
 }
 
@@ -51,7 +52,7 @@ def dist_env():
 
 
 # SymmSpMM right-hand-side counts timed per workload (SURVEY config 3: k = 4, 8, 16)
-SPMM_KS = {"st27_200": (4, 8, 16)}
+SPMM_KS = {"st27_200": (4, 8, 16), "st27_100": (16,)}
 
 
 def max_over_ranks(times, world, device):

@@ -35,6 +35,7 @@ SCHEDULE = {
     "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
     "xxz24": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
     "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_LP, full_launch=_F),
+    "st27_100": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_LP, full_launch=_F),
 }
 
 
