@@ -260,12 +260,10 @@ def run_ours(args):
     s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream)
     build_s = time.perf_counter() - t0
     lc = cfg["launch"]
-    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
-                      lc["regs_per_row"])
+    R.race_set_launch(s, 0, **lc)
     fl = cfg["full_launch"]
     R.race_prepare_full(s, stream)
-    R.race_set_launch(s, 1, fl["executor"], fl["group_lanes"], fl["rows_per_group"], fl["blocks_per_sm"],
-                      fl["regs_per_row"])
+    R.race_set_launch(s, 1, **fl)
     info = s.info()
     perm = s.perm()
     x_host = configs.vectors(name, n)
@@ -325,23 +323,19 @@ def run_ours(args):
     t_leaf_cta = timed(lambda i: R.symm_spmv(s, xs[i % ring], bs[i % ring], stream), 3, 1)
     t_win_race = timed(lambda i: R.symm_spmv_exec(s, R.RACE_EXEC_WINDOW_RACE, xs[i % ring], bs[i % ring], stream),
                        3, 1)
-    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
-                      lc["regs_per_row"])
+    R.race_set_launch(s, 0, **lc)
     # ---- the same two kernels on the input order (no RACE permutation) --------------------
     s_nat = R.race_build(m, cfg["n_workers"], natural_order=True, windows=False, stream=stream)
-    R.race_set_launch(s_nat, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
-                      lc["regs_per_row"])
+    R.race_set_launch(s_nat, 0, **lc)
     R.race_prepare_full(s_nat, stream)
-    R.race_set_launch(s_nat, 1, fl["executor"], fl["group_lanes"], fl["rows_per_group"], fl["blocks_per_sm"],
-                      fl["regs_per_row"])
+    R.race_set_launch(s_nat, 1, **fl)
     t_nat_symm = timed(lambda i: R.symm_spmv(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     t_nat_full = timed(lambda i: R.spmv_full(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     s_nat.free()
     # ---- FP32-stored values (x, b and the row sums stay FP64), same launch -----------------
     s32 = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
                        val_type=R.RACE_F32, windows=False)
-    R.race_set_launch(s32, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
-                      lc["regs_per_row"])
+    R.race_set_launch(s32, 0, **lc)
     t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     # the FP32-valued result for x_host, kept for the normwise error against the FP64 oracle
     with torch.cuda.stream(stream):

@@ -215,6 +215,11 @@ typedef struct {
     int32_t blocks_per_sm;   /* resident 256-thread blocks per SM, 0 = max  */
     int32_t regs_per_row;    /* row entries held in registers by the
                                 pipelined executors: 4, 8 or 16             */
+    int32_t fp64_quarters;   /* RACE_EXEC_DF64_RED (and its SymmSpMM): in
+                                this many quarters of the warps (0..4) the
+                                transposed updates use FP64 multiplies, in
+                                the rest double-float arithmetic; shares the
+                                work between the FP64 and integer pipes  */
 } race_launch;
 
 /* race_set_launch / race_get_launch — which = 0: symm_spmv, which = 1:

@@ -62,7 +62,8 @@ RACE_EXEC_SELL_DF64 = 9
 
 class race_launch(ctypes.Structure):
     _fields_ = [("executor", ctypes.c_int32), ("group_lanes", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("regs_per_row", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("regs_per_row", ctypes.c_int32),
+                ("fp64_quarters", ctypes.c_int32)]
 
 
 class RaceError(RuntimeError):
@@ -295,9 +296,10 @@ def symm_spmv(s: Schedule, x, b, stream=None):
 
 
 def race_set_launch(s: Schedule, which, executor=0, group_lanes=8, rows_per_group=4, blocks_per_sm=0,
-                    regs_per_row=8):
+                    regs_per_row=8, fp64_quarters=0):
     """which = 0: symm_spmv, 1: spmv_full."""
-    lc = race_launch(int(executor), int(group_lanes), int(rows_per_group), int(blocks_per_sm), int(regs_per_row))
+    lc = race_launch(int(executor), int(group_lanes), int(rows_per_group), int(blocks_per_sm), int(regs_per_row),
+                     int(fp64_quarters))
     _check(lib().race_set_launch(s.handle, int(which), ctypes.byref(lc)), "race_set_launch")
 
 

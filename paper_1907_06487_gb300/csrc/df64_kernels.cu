@@ -117,9 +117,13 @@ __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, 
 template <typename VT, int G>
 __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                                     const double* __restrict__ x, double* b) {
+                                                     const double* __restrict__ x, double* b, int fp64_quarters) {
     const int lane = threadIdx.x & (G - 1);
     const unsigned mask = lane_mask<G>();
+    // warps in the first fp64_quarters quarters scatter with FP64 multiplies
+    // (warp-uniform), sharing the work between the FP64 and integer pipes
+    const bool warp64 = ((static_cast<int>(blockIdx.x) * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5)) & 3) <
+                        fp64_quarters;
     const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
     for (int64_t r = gid; r < n; r += ngroups) {
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
         double acc;
         if (st != 0) acc = lane_row<VT, G, kFp64>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
         else if (xrh == 0.0f) acc = lane_row<VT, G, kNone>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        else if (warp64) acc = lane_row<VT, G, kFp64>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
         else acc = lane_row<VT, G, kSplit>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
@@ -155,8 +160,9 @@ void launch_g(const race_schedule* s, const double* x, double* b, cudaStream_t s
     const int64_t per_sm = s->launch.blocks_per_sm > 0 ? s->launch.blocks_per_sm : (2048 / kBlock);
     const int64_t cap = static_cast<int64_t>(sm_count_of_device()) * per_sm;
     const int blocks = static_cast<int>(std::max<int64_t>(1, std::min((threads + kBlock - 1) / kBlock, cap)));
+    const int q64 = s->launch.executor == RACE_EXEC_DF64_RED ? s->launch.fp64_quarters : 0;
     k_symm_df64<VT, G><<<blocks, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, static_cast<const VT*>(s->d_val),
-                                                  x, b);
+                                                  x, b, q64);
 }
 
 template <typename VT>

@@ -414,8 +414,11 @@ template <typename VT, int K, int R, bool DF>
 __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const int32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
                                                             const VT* __restrict__ val, const double* __restrict__ X,
-                                                            double* B) {
+                                                            double* B, int fp64_quarters) {
     const int c = threadIdx.x & (K - 1);
+    // warps in the first fp64_quarters quarters scatter in FP64 (warp-uniform)
+    const bool warp64 = ((static_cast<int>(blockIdx.x) * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5)) & 3) <
+                        fp64_quarters;
     const int64_t grp = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / K;
     const int64_t ngrp = static_cast<int64_t>(gridDim.x) * kBlock / K;
     for (int64_t r0 = grp; r0 < n; r0 += ngrp * R) {
@@ -466,7 +469,9 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
                     acc[q] = fma(a, xc[q][u], acc[q]);
                     if (p + u == 0) continue;  // the diagonal (first entry) has no transposed update
                     if constexpr (DF) {
-                        if (xrh[q] != 0.0f && !df64::is_zero(araw[q][u])) {
+                        if (warp64) {  // warp-uniform: this warp's share of FP64 products
+                            if (!xr64[q]) atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, a * xr[q]);
+                        } else if (xrh[q] != 0.0f && !df64::is_zero(araw[q][u])) {
                             float ah, al, ph, pl;
                             df64::split_value(araw[q][u], ah, al);
                             df64::mul(ah, al, xrh[q], xrl[q], ph, pl);
@@ -698,6 +703,7 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
         const int R = s->launch.rows_per_group >= 4 ? 4 : (s->launch.rows_per_group >= 2 ? 2 : 1);
         const VT* v = static_cast<const VT*>(s->d_val);
         const bool df = s->launch.executor == RACE_EXEC_DF64_RED || s->launch.executor == RACE_EXEC_SELL_DF64;
+        const int q64 = df ? s->launch.fp64_quarters : 0;
         if (df) {
             const int rc = race_df64_prepare(s);
             if (rc) return rc;
@@ -705,9 +711,9 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
 #define RACE_MM_ROWS_DF(KK, DFV)                                                                                   \
     do {                                                                                                           \
         const int g = grid_for((static_cast<int64_t>(n) * KK + R - 1) / R, s->launch.blocks_per_sm);              \
-        if (R == 4) k_symm_mm_rows_red<VT, KK, 4, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);        \
-        else if (R == 2) k_symm_mm_rows_red<VT, KK, 2, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);   \
-        else k_symm_mm_rows_red<VT, KK, 1, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B);               \
+        if (R == 4) k_symm_mm_rows_red<VT, KK, 4, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);        \
+        else if (R == 2) k_symm_mm_rows_red<VT, KK, 2, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);   \
+        else k_symm_mm_rows_red<VT, KK, 1, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);               \
     } while (0)
 #define RACE_MM_ROWS(KK)                 \
     do {                                 \
@@ -861,7 +867,7 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
         l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_SELL_DF64 || l->regs_per_row < 0 ||
-        l->regs_per_row > 16 || (which != 0 && which != 1)) {
+        l->regs_per_row > 16 || l->fp64_quarters < 0 || l->fp64_quarters > 4 || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
     }

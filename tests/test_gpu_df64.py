@@ -215,3 +215,34 @@ def test_natural_order(dev, oracle_mod, matgen_mod, exe):
     x = matgen_mod.uniform(m["n"], 15, -1.0, 1.0)
     bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
     check(run(s, x, dev, exe), bref, sc)
+
+
+@pytest.mark.parametrize("quarters", [1, 2, 4])
+def test_fp64_share_of_transposed_updates(dev, oracle_mod, matgen_mod, quarters):
+    """fp64_quarters: that share of the warps forms its transposed updates with
+    FP64 multiplies, the rest in double-float; same bound either way (SpMV
+    and SpMM, x with zeros and out-of-range entries)."""
+    m = matgen_mod.stencil3d(15, npt=27, seed=9)
+    s = R.race_build(m, 16)
+    R.race_set_launch(s, 0, executor=DF, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4,
+                      fp64_quarters=quarters)
+    n = m["n"]
+    x = matgen_mod.uniform(n, 19, -1.0, 1.0)
+    x[::97] = 0.0
+    x[5::101] = 1.0e25
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
+    check(run(s, x, dev), bref, sc)
+    k = 4
+    X = matgen_mod.uniform(n * k, 20, -1.0, 1.0).reshape(n, k)
+    X[3, 1] = -2.0e22
+    Bref, S = oracle_mod.spmm_full(oracle_mod.expand_full(m), X)
+    perm = s.perm()
+    Xd = torch.from_numpy(np.ascontiguousarray(X[perm])).to(dev)
+    Bd = torch.full_like(Xd, np.nan)
+    R.symm_spmm(s, k, Xd, Bd)
+    torch.cuda.synchronize()
+    Bh = np.empty_like(X)
+    Bh[perm] = Bd.cpu().numpy()
+    check(Bh, Bref, S)
+    with pytest.raises(R.RaceError):
+        R.race_set_launch(s, 0, executor=DF, fp64_quarters=5)

@@ -181,8 +181,7 @@ def test_full_size_xxz26(dev, oracle_mod):
     # the launch the benchmark times (through the default entry point), then
     # the leaf executors
     lc = cfg["launch"]
-    R.race_set_launch(s, 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"], lc["blocks_per_sm"],
-                      lc["regs_per_row"])
+    R.race_set_launch(s, 0, **lc)
     assert_parity(run_symm(s, m, x, dev)[rows], bref, sc)
     for ex in (cfg["executor"], 0):
         b = run_symm(s, m, x, dev, ex)
@@ -207,8 +206,7 @@ def st27_schedule():
         _ST27["m"] = m
         _ST27["s"] = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"])
         lc = cfg["launch"]  # the launch the benchmark times
-        R.race_set_launch(_ST27["s"], 0, lc["executor"], lc["group_lanes"], lc["rows_per_group"],
-                          lc["blocks_per_sm"], lc["regs_per_row"])
+        R.race_set_launch(_ST27["s"], 0, **lc)
     return _ST27["m"], _ST27["s"]
 
 
