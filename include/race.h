@@ -298,8 +298,11 @@ typedef struct race_batch race_batch;  /* opaque */
  * stream) one symm_spmv (k == 1) or symm_spmm (1 < k <= 16) per schedule,
  * with the schedule's current launch shape, on the caller-owned device
  * arrays X_d[i] / B_d[i] (n_i x k row-major, permuted order), into one CUDA
- * graph.  The arrays must stay valid while the batch is used.  The call
- * enqueues nothing; race_batch_launch replays the whole batch.
+ * graph whose matrices run as up to 8 parallel branches (matrices are
+ * independent; each goes to the branch with the least stored work so far,
+ * largest first), forked from and joined into `stream`.  The arrays must
+ * stay valid while the batch is used; two entries must not share an output
+ * array.  The call enqueues nothing; race_batch_launch replays the batch.
  * Errors: RACE_ERR_INVALID, RACE_ERR_CUDA.                                  */
 int race_batch_create(race_schedule *const *s, int32_t count, int32_t k, const double *const *X_d,
                       double *const *B_d, void *stream, race_batch **out);

@@ -33,6 +33,8 @@ int cuda_err(cudaError_t e, const char* what) {
 }
 }  // namespace
 
+constexpr int kBranches = 8;
+
 extern "C" {
 
 int race_batch_create(race_schedule* const* s, int32_t count, int32_t k, const double* const* X_d,
@@ -60,15 +62,56 @@ int race_batch_create(race_schedule* const* s, int32_t count, int32_t k, const d
     if (!b) return RACE_ERR_NOMEM;
     b->count = count;
     b->k = k;
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    // The matrices are independent: the graph runs them as kBranches parallel
+    // branches (forked from and joined into `stream` by events), each matrix
+    // on the branch with the least stored work so far, largest first.
+    const int nb = std::min<int32_t>(kBranches, count);
+    std::vector<cudaStream_t> br(static_cast<size_t>(nb), nullptr);
+    std::vector<cudaEvent_t> ev(static_cast<size_t>(nb) + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < nb && e == cudaSuccess; ++j) e = cudaStreamCreateWithFlags(&br[j], cudaStreamNonBlocking);
+    for (int j = 0; j <= nb && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+    auto release = [&]() {
+        for (cudaStream_t x : br)
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    };
     if (e != cudaSuccess) {
+        release();
+        delete b;
+        return cuda_err(e, "race_batch_create: streams");
+    }
+    std::vector<int32_t> order(static_cast<size_t>(count));
+    for (int32_t i = 0; i < count; ++i) order[static_cast<size_t>(i)] = i;
+    std::stable_sort(order.begin(), order.end(), [s](int32_t a, int32_t c) {
+        return s[a]->h_col.size() > s[c]->h_col.size();
+    });
+    std::vector<int64_t> load(static_cast<size_t>(nb), 0);
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        release();
         delete b;
         return cuda_err(e, "cudaStreamBeginCapture");
     }
     int rc = RACE_OK;
-    for (int32_t i = 0; i < count && rc == RACE_OK; ++i) rc = run_one(s[i], k, X_d[i], B_d[i], st);
+    e = cudaEventRecord(ev[nb], st);
+    for (int j = 0; j < nb && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(br[j], ev[nb], 0);
+    if (e != cudaSuccess) rc = cuda_err(e, "race_batch_create: fork");
+    for (int32_t i : order) {
+        if (rc != RACE_OK) break;
+        const int j = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+        load[static_cast<size_t>(j)] += static_cast<int64_t>(s[i]->h_col.size());
+        rc = run_one(s[i], k, X_d[i], B_d[i], br[j]);
+    }
+    for (int j = 0; j < nb && rc == RACE_OK; ++j) {
+        e = cudaEventRecord(ev[j], br[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[j], 0);
+        if (e != cudaSuccess) rc = cuda_err(e, "race_batch_create: join");
+    }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(st, &g);
+    release();
     if (rc != RACE_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         delete b;
