@@ -178,3 +178,18 @@ def test_natural_order_plan(matgen_mod):
         assert np.array_equal(pm[key], m[key])
     sp, lo, hi = s.phases()
     assert list(sp) == [0, 1] and lo[0] == 0 and hi[0] == m["n"]
+
+
+def test_rejects_sizes_beyond_the_int32_layout(lib):
+    """Maximum sizes: the layout indexes rows and stored entries with int32, so
+    n + nnz >= 2^31 is RACE_ERR_OVERFLOW (checked before any array is read:
+    the arrays passed here are tiny placeholders)."""
+    rp = np.zeros(4, np.int32)
+    col = np.zeros(4, np.int32)
+    val = np.zeros(4)
+    p = R.make_params(4, host_only=True)
+    h = ctypes.c_void_p()
+    for n, nnz in ((3, 2 ** 31), (2 ** 30, 2 ** 30), (2 ** 31 - 1, 1)):
+        a = R.race_csr_upper(n, nnz, rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
+        assert lib.race_build(ctypes.byref(a), ctypes.byref(p), None, ctypes.byref(h)) == R.RACE_ERR_OVERFLOW
+        assert not h.value
