@@ -318,8 +318,8 @@ def run_ours(args):
     # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
     t_full = timed(lambda i: R.spmv_full(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     # ---- the conflict-free RACE executors on the same schedule (a few steps: they are slow),
-    # 8 lanes per row in the leaf executor, then the benchmark's launch again
-    R.race_set_launch(s, 0, R.RACE_EXEC_LEAF_CTA, 8, 1, 0, 8)
+    # one row per thread in the leaf executor, then the benchmark's launch again
+    R.race_set_launch(s, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
     t_leaf_cta = timed(lambda i: R.symm_spmv(s, xs[i % ring], bs[i % ring], stream), 3, 1)
     t_win_race = timed(lambda i: R.symm_spmv_exec(s, R.RACE_EXEC_WINDOW_RACE, xs[i % ring], bs[i % ring], stream),
                        3, 1)

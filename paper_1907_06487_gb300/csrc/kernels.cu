@@ -101,14 +101,24 @@ __global__ void __launch_bounds__(kBlock) k_symm_phase_cta(const int32_t* __rest
             const int32_t rs = __ldg(rp + r), re = __ldg(rp + r + 1);
             const double xr = __ldg(x + r);
             double tmp = 0.0;
-            for (int32_t idx = rs + lane; idx < re; idx += G) {
-                const double a = ldv(val + idx);
-                if (idx == rs) {
-                    tmp += a * xr;
-                } else {
-                    const int32_t c = __ldg(col + idx);
-                    tmp += a * __ldg(x + c);
-                    atomicAdd(b + c, a * xr);
+            // four independent entries per lane and step (loads before uses)
+            for (int32_t idx = rs + lane; idx < re; idx += 4 * G) {
+                double a[4], xc[4];
+                int32_t c[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int32_t j = idx + t * G;
+                    const bool v = j < re;
+                    a[t] = v ? ldv(val + j) : 0.0;
+                    c[t] = v ? __ldg(col + j) : -1;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) xc[t] = c[t] >= 0 ? __ldg(x + c[t]) : 0.0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (c[t] < 0) continue;
+                    tmp = fma(a[t], xc[t], tmp);
+                    if (c[t] != r) atomicAdd(b + c[t], a[t] * xr);
                 }
             }
             tmp = group_sum<G>(tmp, mask);
@@ -652,7 +662,9 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
         default: FN<VT, 32>(s, x, b, st); break;   \
     }
     if (exec == RACE_EXEC_LEAF_CTA) {
-        RACE_DISPATCH(launch_phases_cta)
+        if (s->group_lanes == 1) launch_phases_cta<VT, 1>(s, x, b, st);
+        else if (s->group_lanes == 2) launch_phases_cta<VT, 2>(s, x, b, st);
+        else RACE_DISPATCH(launch_phases_cta)
     } else if (exec == RACE_EXEC_ATOMIC) {
         RACE_DISPATCH(launch_atomic)
     } else if (exec == RACE_EXEC_ROWS_RED || (exec == RACE_EXEC_STREAM_RED && s->max_row_upper > 1024)) {
