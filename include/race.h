@@ -214,7 +214,9 @@ typedef struct {
                                 (RACE_EXEC_ROWS_RED and spmv_full)          */
     int32_t blocks_per_sm;   /* resident 256-thread blocks per SM, 0 = max  */
     int32_t regs_per_row;    /* row entries held in registers by the
-                                pipelined executors: 4, 8 or 16             */
+                                pipelined executors: 4, 8 or 16; entries
+                                per lane and step of RACE_EXEC_DF64_RED
+                                (4, or 8 when >= 8)                         */
     int32_t fp64_quarters;   /* RACE_EXEC_DF64_RED (and its SymmSpMM): in
                                 this many quarters of the warps (0..4) the
                                 transposed updates use FP64 multiplies, in

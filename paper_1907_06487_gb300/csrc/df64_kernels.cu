@@ -72,28 +72,28 @@ __global__ void k_check_offdiag(int32_t n, const int32_t* __restrict__ rp, const
 enum Scatter { kSplit = 0, kFp64 = 1, kNone = 2 };
 
 // One row's share of one lane: FP64 row sum returned, transposed updates
-// sent to b.  Four independent entries per lane and iteration.
-template <typename VT, int G, int MODE>
+// sent to b.  B (4 or 8) independent entries per lane and iteration.
+template <typename VT, int G, int MODE, int B>
 __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, int lane,
                                            const int32_t* __restrict__ col, const VT* __restrict__ val,
                                            const double* __restrict__ x, double* b, double xr, float xrh,
                                            float xrl) {
     double acc = 0.0;
-    for (int32_t idx = lo + lane; idx < hi; idx += 4 * G) {
-        VT a[4];
-        int32_t c[4];
-        double xc[4];
+    for (int32_t idx = lo + lane; idx < hi; idx += B * G) {
+        VT a[B];
+        int32_t c[B];
+        double xc[B];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < B; ++t) {
             const int32_t j = idx + t * G;
             const bool v = j < hi;
             a[t] = v ? __ldg(val + j) : VT(0);
             c[t] = v ? __ldg(col + j) : -1;
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) xc[t] = c[t] >= 0 ? __ldg(x + c[t]) : 0.0;
+        for (int t = 0; t < B; ++t) xc[t] = c[t] >= 0 ? __ldg(x + c[t]) : 0.0;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < B; ++t) {
             if (c[t] < 0) continue;
             acc = fma(df64::widen(a[t]), xc[t], acc);
             if constexpr (MODE == kSplit) {
@@ -114,7 +114,7 @@ __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, 
 // G lanes per row, rows strided over the grid; the lanes' FP64 row sums are
 // combined by shuffles and go to b[row] as a reduction at L2 (b is zeroed
 // first; transposed updates of other rows land there too).
-template <typename VT, int G>
+template <typename VT, int G, int B>
 __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const VT* __restrict__ val,
                                                      const double* __restrict__ x, double* b, int fp64_quarters) {
@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
         float xrh, xrl;
         const int st = df64::split(xr, xrh, xrl);
         double acc;
-        if (st != 0) acc = lane_row<VT, G, kFp64>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-        else if (xrh == 0.0f) acc = lane_row<VT, G, kNone>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-        else if (warp64) acc = lane_row<VT, G, kFp64>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-        else acc = lane_row<VT, G, kSplit>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        if (st != 0) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        else if (xrh == 0.0f) acc = lane_row<VT, G, kNone, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        else if (warp64) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+        else acc = lane_row<VT, G, kSplit, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
         if (lane == 0) atomicAdd(b + row, acc);
@@ -160,9 +160,13 @@ void launch_g(const race_schedule* s, const double* x, double* b, cudaStream_t s
     const int64_t per_sm = s->launch.blocks_per_sm > 0 ? s->launch.blocks_per_sm : (2048 / kBlock);
     const int64_t cap = static_cast<int64_t>(sm_count_of_device()) * per_sm;
     const int blocks = static_cast<int>(std::max<int64_t>(1, std::min((threads + kBlock - 1) / kBlock, cap)));
-    const int q64 = s->launch.executor == RACE_EXEC_DF64_RED ? s->launch.fp64_quarters : 0;
-    k_symm_df64<VT, G><<<blocks, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, static_cast<const VT*>(s->d_val),
-                                                  x, b, q64);
+    const bool mine = s->launch.executor == RACE_EXEC_DF64_RED;
+    const int q64 = mine ? s->launch.fp64_quarters : 0;
+    const VT* v = static_cast<const VT*>(s->d_val);
+    if (mine && s->launch.regs_per_row >= 8)
+        k_symm_df64<VT, G, 8><<<blocks, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, v, x, b, q64);
+    else
+        k_symm_df64<VT, G, 4><<<blocks, kBlock, 0, st>>>(s->plan.n, s->d_rp, s->d_col, v, x, b, q64);
 }
 
 template <typename VT>

@@ -51,11 +51,13 @@ def check(b, bref, sc):
     assert np.all(err <= bound), f"row {worst}: err {err[worst]:.3e} > {bound[worst]:.3e}"
 
 
+@pytest.mark.parametrize("per_step", [4, 8])
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
-def test_lanes(dev, oracle_mod, matgen_mod, lanes):
+def test_lanes(dev, oracle_mod, matgen_mod, lanes, per_step):
     m = matgen_mod.stencil3d(21, npt=27, seed=8)
     s = R.race_build(m, 32)
-    R.race_set_launch(s, 0, executor=DF, group_lanes=lanes, rows_per_group=1, blocks_per_sm=0, regs_per_row=4)
+    R.race_set_launch(s, 0, executor=DF, group_lanes=lanes, rows_per_group=1, blocks_per_sm=0,
+                      regs_per_row=per_step, fp64_quarters=1)
     x = matgen_mod.uniform(m["n"], 31, -1.0, 1.0)
     bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
     check(run(s, x, dev), bref, sc)
