@@ -317,13 +317,16 @@ def run_ours(args):
     t_red, t_col = probe(0), probe(1)
     # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
     t_full = timed(lambda i: R.spmv_full(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
-    # ---- the conflict-free RACE executors on the same schedule (a few steps: they are slow),
-    # one row per thread in the leaf executor, then the benchmark's launch again
-    R.race_set_launch(s, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
-    t_leaf_cta = timed(lambda i: R.symm_spmv(s, xs[i % ring], bs[i % ring], stream), 3, 1)
-    t_win_race = timed(lambda i: R.symm_spmv_exec(s, R.RACE_EXEC_WINDOW_RACE, xs[i % ring], bs[i % ring], stream),
-                       3, 1)
-    R.race_set_launch(s, 0, **lc)
+    # ---- the conflict-free RACE executors (a few steps: they are slow) on the schedule that
+    # suits them (full recursion), one row per thread in the leaf executor
+    cf = cfg["conflict_free"]
+    s_cf = R.race_build(m, cf["n_workers"], eps=cfg["eps"], max_depth=cf["max_depth"], stream=stream)
+    info_cf = s_cf.info()
+    R.race_set_launch(s_cf, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
+    t_leaf_cta = timed(lambda i: R.symm_spmv(s_cf, xs[i % ring], bs[i % ring], stream), 3, 1)
+    t_win_race = timed(lambda i: R.symm_spmv_exec(s_cf, R.RACE_EXEC_WINDOW_RACE, xs[i % ring], bs[i % ring],
+                                                  stream), 3, 1)
+    s_cf.free()
     # ---- the same two kernels on the input order (no RACE permutation) --------------------
     s_nat = R.race_build(m, cfg["n_workers"], natural_order=True, windows=False, stream=stream)
     R.race_set_launch(s_nat, 0, **lc)
@@ -465,9 +468,12 @@ def run_ours(args):
                           "what": "the same launches on the input order (RACE_FLAG_NATURAL_ORDER: no permutation)"},
         "race_conflict_free": {"leaf_cta_ms_per_step": t_leaf_cta / 3 * 1e3,
                                "window_race_ms_per_step": t_win_race / 3 * 1e3,
-                               "n_workers": cfg["n_workers"], "n_phases": info["n_phases"],
+                               "schedule": {"n_workers": cf["n_workers"], "max_depth": cf["max_depth"],
+                                            "n_phases": info_cf["n_phases"], "n_leaves": info_cf["n_leaves"],
+                                            "eta": info_cf["eta"]},
                                "what": "RACE_EXEC_LEAF_CTA and RACE_EXEC_WINDOW_RACE (phase by phase, no two concurrent "
-                                       "leaves share an entry of b) on the benchmark schedule, 3 steps each"},
+                                       "leaves share an entry of b; x and b in that schedule's order) on a fully "
+                                       "recursed schedule, 3 steps each"},
         "speedup_vs_full": t_full / t_symm,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
@@ -512,7 +518,8 @@ def run_batch(args):
     sym_bytes = 0
     tuned = {}
     for i, m in enumerate(mats):
-        s = R.race_build(m, 64, stream=stream)
+        s = R.race_build(m, configs.BATCH_SCHEDULE["n_workers"], max_depth=configs.BATCH_SCHEDULE["max_depth"],
+                         stream=stream)
         n, nu = m["n"], len(m["col"])
         X = configs.matgen.uniform(n * k, 300 + i).reshape(n, k)
         xp = torch.from_numpy(np.ascontiguousarray(X[s.perm()])).to(dev)

@@ -26,17 +26,32 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # tested at full size, and the launch shapes of symm_spmv / spmv_full
 # (shapes from the measured sweeps on GB300: one row per thread wins; FP64
 # row sums with double-float transposed updates are at least as fast as
-# all-FP64 on every workload, 9 % faster on the 27-point stencil)
+# all-FP64 on every workload).  The recursion stops after stage 1 (two
+# colours of level groups, Sec. 4.4.3): the executors that take the
+# transposed update through L2 reductions use the schedule's permutation,
+# not its phases, and the stage-0 level order keeps neighbours close while
+# deeper sub-level orders scatter them (XXZ L=26: 0.34 ms at depth 1
+# against 0.43 ms at unlimited depth; the 27-point stencil is indifferent).
+# The conflict-free executors need the full recursion's balance instead:
+# `conflict_free` is the schedule they are measured on (the fastest of the
+# measured N_t sweep that builds in seconds).
 _L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=8, fp64_quarters=2)
 _LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=8, fp64_quarters=2)
 _F = dict(executor=2, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=16)
 SCHEDULE = {
     "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
-    "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
-    "xxz24": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
-    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_LP, full_launch=_F),
-    "st27_100": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_LP, full_launch=_F),
+    "xxz26": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, executor=1, launch=_L, full_launch=_F,
+                  conflict_free=dict(n_workers=152, max_depth=-1)),
+    "xxz24": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, executor=1, launch=_L, full_launch=_F,
+                  conflict_free=dict(n_workers=152, max_depth=-1)),
+    "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, executor=1, launch=_LP, full_launch=_F,
+                     conflict_free=dict(n_workers=2432, max_depth=-1)),
+    "st27_100": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, executor=1, launch=_LP, full_launch=_F,
+                     conflict_free=dict(n_workers=2432, max_depth=-1)),
 }
+
+# schedule of every matrix of the batch workload (same reasoning as above)
+BATCH_SCHEDULE = dict(n_workers=64, max_depth=1)
 
 
 def batch64(count: int = 64, scale: float = 1.0) -> list:

@@ -193,3 +193,17 @@ def test_rejects_sizes_beyond_the_int32_layout(lib):
         a = R.race_csr_upper(n, nnz, rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
         assert lib.race_build(ctypes.byref(a), ctypes.byref(p), None, ctypes.byref(h)) == R.RACE_ERR_OVERFLOW
         assert not h.value
+
+
+@pytest.mark.parametrize("name", ["xxz26", "st27_200"])
+def test_full_size_schedules_match_oracle(oracle_mod, name):
+    """The benchmark's schedules at full size (XXZ L=26: 10.4 M rows; 27-point
+    200^3: 8 M rows), built by the library on the host and by the oracle:
+    identical byte images (permutation, phases, leaves, tree, eta)."""
+    from paper_1907_06487_gb300 import configs
+    m = configs.matrix(name)
+    cfg = configs.SCHEDULE[name]
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], host_only=True)
+    o = oracle_mod.Race(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"])
+    assert s.export() == o.export()
+    s.free()
