@@ -35,8 +35,8 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # The conflict-free executors need the full recursion's balance instead:
 # `conflict_free` is the schedule they are measured on (the fastest of the
 # measured N_t sweep that builds in seconds).
-_L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=8, fp64_quarters=2)
-_LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=8, fp64_quarters=2)
+_L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=5, regs_per_row=4, fp64_quarters=2)
+_LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=8, fp64_quarters=2)
 _F = dict(executor=2, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=16)
 SCHEDULE = {
     "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),
