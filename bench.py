@@ -51,7 +51,7 @@ def dist_env():
     return rank, world, local
 
 
-# SymmSpMM right-hand-side counts timed per workload (SURVEY config 3: k = 4, 8, 16)
+# SymmSpMM right-hand-side counts timed per workload (the 27-point stencil: k = 4, 8, 16)
 SPMM_KS = {"st27_200": (4, 8, 16), "st27_100": (16,)}
 
 

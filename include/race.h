@@ -292,7 +292,7 @@ int race_get_info(const race_schedule *s, race_info *info);
  * n_sublevels, n_children, phase_count, phase_offset; int64 size, neff.    */
 int race_export(const race_schedule *s, void *buf, size_t *size);
 
-/* ---- batches and tuning (spec: many matrices of uneven size in one
+/* ---- batches and tuning (beyond the paper: many matrices of uneven size in one
  * captured graph; launch shapes picked by an autotuner) ------------------- */
 typedef struct race_batch race_batch;  /* opaque */
 
@@ -322,7 +322,7 @@ void race_batch_free(race_batch *b);
 int race_autotune(race_schedule *s, int32_t k, const double *X_d, double *B_d, int32_t reps, void *stream,
                   race_launch *best, float *best_us);
 
-/* ---- learned RACE-parameter predictor (north star; the paper picks the
+/* ---- learned RACE-parameter predictor (beyond the paper, which picks the
  * epsilon_s by a parameter study, Sec. 5.1) ------------------------------- */
 
 /* race_features — 16 FP32 features of an upper-triangle CRS (host memory,
