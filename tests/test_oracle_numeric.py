@@ -193,3 +193,28 @@ def test_threaded_full_spmv(oracle_mod, matgen_mod):
     for t in (1, 4):
         assert np.array_equal(oracle_mod.spmv_full_par(full, x, t), b)
     assert oracle_mod.max_threads() >= 1
+
+
+def test_oracle_error_within_the_recursive_summation_bound(oracle_mod, matgen_mod):
+    """The oracle's own FP64 error, against exact rational arithmetic: every
+    row of b = A x stays within gamma_m * s_i (m = the row's length,
+    gamma_m = m u / (1 - m u), u = 2^-53; Higham, "Accuracy and Stability of
+    Numerical Algorithms", Sec. 3.1), far below the 1e-12 * s_i parity bound
+    the GPU path is held to."""
+    from fractions import Fraction
+    m = matgen_mod.stencil3d(7, npt=27, seed=11)
+    full = oracle_mod.expand_full(m)
+    x = matgen_mod.uniform(m["n"], 12, -1.0, 1.0)
+    b, s = oracle_mod.spmv_full(full, x)
+    rp, col, val = full["row_ptr"], full["col"], full["val"]
+    u = Fraction(1, 2 ** 53)
+    worst = 0.0
+    for i in range(m["n"]):
+        lo, hi = int(rp[i]), int(rp[i + 1])
+        exact = sum(Fraction(float(val[j])) * Fraction(float(x[col[j]])) for j in range(lo, hi))
+        mlen = hi - lo
+        gamma = mlen * u / (1 - mlen * u)
+        err = abs(Fraction(float(b[i])) - exact)
+        assert err <= gamma * Fraction(float(s[i])) * (1 + 2 * u) + Fraction(1, 2 ** 1074)
+        worst = max(worst, float(err / Fraction(float(s[i]))) if s[i] else 0.0)
+    assert worst < 1e-15
