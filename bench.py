@@ -352,11 +352,15 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             Xk = [torch.rand(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
             Bk = [torch.empty(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+        # the project's autotuner picks this k's launch shape, then the timed steps run it
+        tuned, _ = R.race_autotune(s, k, Xk[0], Bk[0], reps=3, stream=stream)
         tk = timed(lambda i: R.symm_spmm(s, k, Xk[i % 2], Bk[i % 2], stream), max(3, args.steps // 4), 2)
         per_k = tk / max(3, args.steps // 4)
         spmm[str(k)] = {"ms_per_step": per_k * 1e3, "gflops": pm.flops(nf, k) / per_k / 1e9,
-                        "gbs": pm.symm_bytes(n, nu, k) / per_k / 1e9}
+                        "gbs": pm.symm_bytes(n, nu, k) / per_k / 1e9, "launch": tuned}
         del Xk, Bk
+    if spmm:
+        R.race_set_launch(s, 0, **lc)  # the SymmSpMV launch again
     # ---- end to end through host buffers: H2D x, permute, SymmSpMV, unpermute, D2H b --------
     # Each step copies its x in and its b out; copies run on their own streams
     # (double-buffered), so step i's read-back overlaps step i+1's upload and
