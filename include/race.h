@@ -66,6 +66,18 @@ extern "C" {
                                    row.  For comparisons on the input order
                                    (the row-parallel executors run as usual;
                                    the leaf executors then run serially).   */
+#define RACE_FLAG_PSEUDO_PERIPHERAL 8u /* stage-0 roots: instead of the last
+                                   unvisited vertex itself, a pseudo-
+                                   peripheral vertex of its connected
+                                   component (George and Liu's iteration,
+                                   ACM TOMS 5, 1979: BFS, take a vertex of
+                                   minimum degree in the deepest level, lowest
+                                   index on ties, repeat while the
+                                   eccentricity grows).  The paper's inputs
+                                   are RCM-ordered, whose last row is such a
+                                   vertex (Sec. 6.1); this flag gives other
+                                   orders the same start.  Recursion roots
+                                   are unchanged.                           */
 
 /* Upper-triangle CRS matrix in HOST memory (Sec. 3.2, Alg. "SymmSpMV"):
  * row i holds the entries (i, j) with j >= i.  Columns may come in any
@@ -291,6 +303,23 @@ int race_get_info(const race_schedule *s, race_info *info);
  * stage, color, lo, hi, n_threads, thread_lo, n_levels_in_parent,
  * n_sublevels, n_children, phase_count, phase_offset; int64 size, neff.    */
 int race_export(const race_schedule *s, void *buf, size_t *size);
+
+/* race_import — a schedule rebuilt from a race_export image and the matrix
+ * it was built from, without running the construction of Sec. 4 again (a
+ * schedule cache: the construction takes seconds on large matrices, the
+ * import one pass over the matrix).  The matrix is canonicalised and
+ * permuted by the image's permutation; the image is checked entirely:
+ * header, sizes, permutation, phase offsets, leaves covering every row
+ * exactly once, the tree's shape, and that no two leaves of one phase update
+ * the same entry of b on this matrix (the distance-2 condition of Sec. 4.2).
+ * image/size: caller-owned bytes, only read.  flags: RACE_FLAG_HOST_ONLY and
+ * RACE_FLAG_NO_WINDOWS, as for race_build.  The launch shape starts at the
+ * defaults of race_build and group_lanes is automatic.  race_export of the
+ * result reproduces the image byte for byte.
+ * Errors: RACE_ERR_INVALID (malformed image, or an image of another
+ * matrix; reason in race_last_error_detail), _OVERFLOW, _NOMEM, _CUDA.      */
+int race_import(const race_csr_upper *a, const void *image, size_t size, uint32_t flags, void *stream,
+                race_schedule **out);
 
 /* ---- batches and tuning (beyond the paper: many matrices of uneven size in one
  * captured graph; launch shapes picked by an autotuner) ------------------- */

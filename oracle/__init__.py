@@ -73,7 +73,7 @@ def _get():
     L.orc_canonicalize.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p]
     L.orc_race.restype = ctypes.c_void_p
     L.orc_race.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _f64p, ctypes.c_int32,
-                           ctypes.c_int32]
+                           ctypes.c_int32, ctypes.c_int32]
     L.orc_race_free.argtypes = [ctypes.c_void_p]
     L.orc_race_info.argtypes = [ctypes.c_void_p, _i32p, _f64p]
     L.orc_race_perm.argtypes = [ctypes.c_void_p, _i32p]
@@ -87,6 +87,8 @@ def _get():
     L.orc_check_phases.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p]
     L.orc_bfs_dist.restype = ctypes.c_int
     L.orc_bfs_dist.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _i32p]
+    L.orc_pseudo_peripheral.restype = ctypes.c_int32
+    L.orc_pseudo_peripheral.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32]
     _lib = L
     return L
 
@@ -211,17 +213,23 @@ def bfs_dist(m, root):
     return d
 
 
+def pseudo_peripheral(m, start):
+    """George and Liu's pseudo-peripheral vertex reached from `start`."""
+    n, rp, ci, _ = _mat(m)
+    return int(_get().orc_pseudo_peripheral(n, _p(rp, _i32p), _p(ci, _i32p), int(start)))
+
+
 class Race:
     """The oracle's RACE schedule for one matrix (Sec. 4-5 of the paper)."""
 
-    def __init__(self, m, n_workers, eps=DEFAULT_EPS, max_depth=-1, balance=0):
+    def __init__(self, m, n_workers, eps=DEFAULT_EPS, max_depth=-1, balance=0, pseudo_peripheral=False):
         n, rp, ci, _ = _mat(m)
         e = np.zeros(8)
         e[:len(eps)] = eps
         if len(eps) < 8:
             e[len(eps):] = eps[-1]
         self._h = _get().orc_race(n, _p(rp, _i32p), _p(ci, _i32p), int(n_workers), _p(e, _f64p),
-                                  int(max_depth), int(balance))
+                                  int(max_depth), int(balance), int(bool(pseudo_peripheral)))
         if not self._h:
             raise ValueError("oracle race build failed")
         info = np.zeros(6, np.int32)

@@ -35,7 +35,10 @@
  * Readings taken where the paper is silent or garbled (each one is listed
  * in the design notes of the repository):
  *   R1 root of a (sub)graph = its last vertex in the current order
- *      (Alg. "Construction of levels" sets root = n).
+ *      (Alg. "Construction of levels" sets root = n).  Opt-in: stage-0
+ *      roots become a pseudo-peripheral vertex of their component
+ *      (George and Liu, ACM TOMS 5, 1979), the start node of the RCM
+ *      orderings the paper's inputs carry (Sec. 6.1).
  *   R2 BFS runs until the frontier is empty; unvisited vertices of the group
  *      restart from the last unvisited one at (max level so far) + 2
  *      (islands, Sec. 4.4.1).
@@ -286,7 +289,7 @@ typedef struct {
 } onode;
 
 typedef struct {
-    int32_t n, nt, k, balance, max_depth;
+    int32_t n, nt, k, balance, max_depth, pp;
     double eps[8];
     /* graph: full adjacency without self loops */
     int64_t *aptr; int32_t *adj;
@@ -315,6 +318,51 @@ static int32_t new_node(osched *S) {
     return S->nnodes++;
 }
 
+/* Breadth-first search over the whole graph from r: returns the
+ * eccentricity of r and lists the vertices at that distance in far[0..*nfar).
+ * dist must hold -1 everywhere on entry and does so again on return.     */
+static int32_t ecc_from(const int64_t *aptr, const int32_t *adj, int32_t r, int32_t *dist, int32_t *queue,
+                        int32_t *far, int32_t *nfar) {
+    int32_t head = 0, tail = 0, ecc = 0;
+    dist[r] = 0; queue[tail++] = r;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        if (dist[u] > ecc) ecc = dist[u];
+        for (int64_t e = aptr[u]; e < aptr[u + 1]; ++e)
+            if (dist[adj[e]] < 0) { dist[adj[e]] = dist[u] + 1; queue[tail++] = adj[e]; }
+    }
+    *nfar = 0;
+    for (int32_t q = 0; q < tail; ++q) if (dist[queue[q]] == ecc) far[(*nfar)++] = queue[q];
+    for (int32_t q = 0; q < tail; ++q) dist[queue[q]] = -1;
+    return ecc;
+}
+
+/* George and Liu's pseudo-peripheral node finder: from the start r, pick
+ * the vertex x of minimum degree (smallest index on ties) among the
+ * vertices farthest from r; if x is farther from its own farthest vertices
+ * than r is, continue from x, else r is the answer.                        */
+static int32_t pseudo_peripheral(int32_t n, const int64_t *aptr, const int32_t *adj, int32_t r) {
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *far = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) dist[i] = -1;
+    int32_t nfar = 0;
+    int32_t ecc_r = ecc_from(aptr, adj, r, dist, queue, far, &nfar);
+    for (;;) {
+        int32_t x = far[0];
+        for (int32_t q = 1; q < nfar; ++q) {
+            int32_t w = far[q];
+            int64_t dw = aptr[w + 1] - aptr[w], dx = aptr[x + 1] - aptr[x];
+            if (dw < dx || (dw == dx && w < x)) x = w;
+        }
+        int32_t ecc_x = ecc_from(aptr, adj, x, dist, queue, far, &nfar);
+        if (ecc_x <= ecc_r) break;
+        r = x; ecc_r = ecc_x;
+    }
+    free(dist); free(queue); free(far);
+    return r;
+}
+
 /* Level construction on the group order[lo..hi) (Alg. "Construction of
  * levels", Eq. "level"), restricted to the group plus its distance-1 halo
  * unless whole_graph.  Rewrites order[lo..hi) level by level (R3) and
@@ -334,6 +382,7 @@ static int32_t build_levels(osched *S, int32_t lo, int32_t hi, int whole_graph,
     while (remaining > 0) {
         while (S->dmark[S->order[scan]] == st) --scan;       /* R1/R2 */
         int32_t root = S->order[scan];
+        if (whole_graph && S->pp) root = pseudo_peripheral(S->n, S->aptr, S->adj, root);
         int32_t lvl = (maxlvl < 0) ? 0 : maxlvl + 2;
         S->dmark[root] = st; S->dist[root] = lvl;
         if (S->tmark[root] == st) --remaining;
@@ -590,10 +639,11 @@ static int cmp_leaf(const void *a, const void *b) {
 void orc_race_free(osched *S);
 
 osched *orc_race(int32_t n, const int32_t *rp, const int32_t *ci, int32_t nt, const double *eps8,
-                 int32_t max_depth, int32_t balance) {
+                 int32_t max_depth, int32_t balance, int32_t pseudo_peripheral_root) {
     if (n <= 0 || nt <= 0) return NULL;
     osched *S = (osched *)calloc(1, sizeof(osched));
     S->n = n; S->nt = nt; S->k = 2; S->balance = balance; S->max_depth = max_depth;
+    S->pp = pseudo_peripheral_root != 0;
     for (int i = 0; i < 8; ++i) S->eps[i] = eps8[i];
     /* symmetric adjacency (self loops dropped, Sec. 4 graph definitions) */
     S->aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -786,6 +836,25 @@ int orc_check_phases(int32_t n, const int32_t *prp, const int32_t *pci, int32_t 
     for (int32_t i = 0; i < n && !rc; ++i) if (cover[i] != 1) rc = 1;
     free(cover); free(owner); free(ophase);
     return rc;
+}
+
+/* The pseudo-peripheral vertex reached from `start` on the symmetric graph
+ * of an upper CRS (self loops dropped).                                   */
+int32_t orc_pseudo_peripheral(int32_t n, const int32_t *rp, const int32_t *ci, int32_t start) {
+    int64_t *aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { aptr[i + 1]++; aptr[ci[t] + 1]++; }
+    for (int32_t i = 0; i < n; ++i) aptr[i + 1] += aptr[i];
+    int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(aptr[n] > 0 ? aptr[n] : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    memcpy(fill, aptr, sizeof(int64_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { adj[fill[i]++] = ci[t]; adj[fill[ci[t]]++] = i; }
+    int32_t r = pseudo_peripheral(n, aptr, adj, start);
+    free(fill); free(adj); free(aptr);
+    return r;
 }
 
 /* Plain BFS distances on the whole graph from one root (Eq. "level").    */

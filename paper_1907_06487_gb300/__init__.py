@@ -7,7 +7,7 @@ import of ``lib()`` raises.
 
 Names follow the C ABI in ``include/race.h``:
 ``race_build``, ``symm_spmv``, ``symm_spmm``, ``spmv_full``, ``race_permute``,
-``race_unpermute``, ``race_get_info``, ``race_export``, ``race_free``.
+``race_unpermute``, ``race_get_info``, ``race_export``, ``race_import``, ``race_free``.
 Device arrays may be torch CUDA tensors (anything with ``data_ptr()``) or raw
 integer addresses; streams may be ``torch.cuda.Stream`` objects, raw handles
 or None (legacy default stream).
@@ -36,6 +36,7 @@ RACE_BAL_NNZ = 1
 RACE_FLAG_HOST_ONLY = 1
 RACE_FLAG_NO_WINDOWS = 2
 RACE_FLAG_NATURAL_ORDER = 4
+RACE_FLAG_PSEUDO_PERIPHERAL = 8
 
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
@@ -46,7 +47,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status", "race_probe_scatter",
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
-            "race_mlp_backward", "race_mlp_adam", "race_upload")
+            "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -127,6 +128,8 @@ def lib():
     L.race_get_phases.argtypes = [vp, vp, vp, vp]
     L.race_get_info.argtypes = [vp, ctypes.POINTER(race_info)]
     L.race_export.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.race_import.argtypes = [ctypes.POINTER(race_csr_upper), vp, ctypes.c_size_t, ctypes.c_uint32, vp,
+                              ctypes.POINTER(vp)]
     L.race_set_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
     L.race_get_launch.argtypes = [vp, i32, ctypes.POINTER(race_launch)]
     L.race_set_launch.restype = ctypes.c_int
@@ -171,7 +174,7 @@ def lib():
     L.race_last_error_detail.restype = ctypes.c_char_p
     for name in ("race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full", "race_prepare_full", "race_permute",
                  "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases", "race_get_info",
-                 "race_export"):
+                 "race_export", "race_import"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -203,7 +206,7 @@ def _check(rc, where):
 
 
 def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False,
-                windows=True, natural_order=False):
+                windows=True, natural_order=False, pseudo_peripheral=False):
     p = race_params()
     lib().race_default_params(ctypes.byref(p), int(n_workers))
     e = list(eps) + [eps[-1]] * (8 - len(eps))
@@ -213,7 +216,8 @@ def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, g
     p.balance = int(balance)
     p.group_lanes = int(group_lanes)
     p.flags = ((RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
-               | (RACE_FLAG_NATURAL_ORDER if natural_order else 0))
+               | (RACE_FLAG_NATURAL_ORDER if natural_order else 0)
+               | (RACE_FLAG_PSEUDO_PERIPHERAL if pseudo_peripheral else 0))
     return p
 
 
@@ -276,19 +280,41 @@ class Schedule:
             pass
 
 
-def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
-               host_only=False, stream=None, val_type=RACE_F64, windows=True, natural_order=False) -> Schedule:
-    """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
+def _csr(m, val_type):
+    """race_csr_upper over host arrays; the arrays are returned too and must
+    outlive the struct."""
     n = int(m["n"])
     rp = np.ascontiguousarray(m["row_ptr"], dtype=np.int32)
     col = np.ascontiguousarray(m["col"], dtype=np.int32)
     val = np.ascontiguousarray(m["val"], dtype=np.float64 if val_type == RACE_F64 else np.float32)
     a = race_csr_upper(n, int(rp[-1]) if n > 0 else 0, rp.ctypes.data, col.ctypes.data if len(col) else None,
                        val.ctypes.data if len(val) else None, int(val_type))
-    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows, natural_order)
+    return a, (rp, col, val)
+
+
+def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
+               host_only=False, stream=None, val_type=RACE_F64, windows=True, natural_order=False,
+               pseudo_peripheral=False) -> Schedule:
+    """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
+    a, keep = _csr(m, val_type)
+    p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows, natural_order,
+                    pseudo_peripheral)
     h = ctypes.c_void_p()
     _check(lib().race_build(ctypes.byref(a), ctypes.byref(p), _stream(stream), ctypes.byref(h)), "race_build")
-    return Schedule(h.value, n)
+    del keep
+    return Schedule(h.value, a.n)
+
+
+def race_import(m, image: bytes, host_only=False, stream=None, val_type=RACE_F64, windows=True) -> Schedule:
+    """race_import: the schedule of a race_export image, on the matrix it was built from."""
+    a, keep = _csr(m, val_type)
+    buf = (ctypes.c_uint8 * len(image)).from_buffer_copy(image) if len(image) else (ctypes.c_uint8 * 1)()
+    flags = (RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
+    h = ctypes.c_void_p()
+    _check(lib().race_import(ctypes.byref(a), buf, len(image), flags, _stream(stream), ctypes.byref(h)),
+           "race_import")
+    del keep
+    return Schedule(h.value, a.n)
 
 
 def symm_spmv(s: Schedule, x, b, stream=None):

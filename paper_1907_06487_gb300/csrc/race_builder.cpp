@@ -14,7 +14,9 @@
 //      flattening of the tree into globally synchronised phases for the GPU.
 //
 // Interpretation choices where the paper is silent or garbled:
-//   - root = last vertex of the (sub)graph in its current order;
+//   - root = last vertex of the (sub)graph in its current order (with
+//     RACE_FLAG_PSEUDO_PERIPHERAL, stage-0 roots move to a pseudo-peripheral
+//     vertex of their component);
 //   - islands restart from the last unvisited group vertex at level
 //     (highest level reached so far) + 2;
 //   - vertices of one level keep their current relative order;
@@ -141,7 +143,8 @@ private:
         std::vector<int32_t> front, next;
         while (left > 0) {
             do { --cursor; } while (seen_[seq_[cursor]] == s);
-            const int32_t root = seq_[cursor];
+            const int32_t root = (whole && (p_.flags & RACE_FLAG_PSEUDO_PERIPHERAL)) ? pseudo_peripheral(seq_[cursor])
+                                                                                     : seq_[cursor];
             int32_t lev = top < 0 ? 0 : top + 2;
             seen_[root] = s;
             depth_of_[root] = lev;
@@ -185,6 +188,52 @@ private:
         }
         std::copy(scratch_.begin(), scratch_.end(), seq_.begin() + lo);
         return ls;
+    }
+
+    // Eccentricity of v in the whole graph; `far` receives the vertices at
+    // that distance (in BFS order).
+    int32_t eccentricity(int32_t v, std::vector<int32_t>& far) {
+        if (pp_mark_.empty()) pp_mark_.assign(static_cast<size_t>(n_), 0);
+        const uint32_t s = ++pp_stamp_;
+        std::vector<int32_t> front(1, v), next;
+        pp_mark_[static_cast<size_t>(v)] = s;
+        int32_t ecc = 0;
+        for (;;) {
+            next.clear();
+            for (int32_t u : front)
+                for (int64_t e = g_.off[u]; e < g_.off[u + 1]; ++e) {
+                    const int32_t w = g_.nbr[e];
+                    if (pp_mark_[static_cast<size_t>(w)] == s) continue;
+                    pp_mark_[static_cast<size_t>(w)] = s;
+                    next.push_back(w);
+                }
+            if (next.empty()) break;
+            front.swap(next);
+            ++ecc;
+        }
+        far.swap(front);
+        return ecc;
+    }
+
+    // George and Liu's pseudo-peripheral vertex of v's connected component:
+    // from the current start, take a vertex of minimum degree (lowest index
+    // on ties) among those farthest away; move there while its eccentricity
+    // is larger, stop at the first start that is not beaten.
+    int32_t pseudo_peripheral(int32_t v) {
+        std::vector<int32_t> far, far_u;
+        int32_t ecc = eccentricity(v, far);
+        for (;;) {
+            int32_t u = far[0];
+            for (int32_t w : far) {
+                const int64_t dw = g_.off[w + 1] - g_.off[w], du = g_.off[u + 1] - g_.off[u];
+                if (dw < du || (dw == du && w < u)) u = w;
+            }
+            const int32_t ecc_u = eccentricity(u, far_u);
+            if (ecc_u <= ecc) return v;
+            v = u;
+            ecc = ecc_u;
+            far.swap(far_u);
+        }
     }
 
     struct Pair {
@@ -418,6 +467,8 @@ private:
     std::vector<int32_t> depth_of_;
     std::vector<int32_t> scratch_;
     uint32_t stamp_ = 0;
+    std::vector<uint32_t> pp_mark_;  // BFS stamps of the pseudo-peripheral search
+    uint32_t pp_stamp_ = 0;
 };
 
 template <typename T>
@@ -495,6 +546,105 @@ std::vector<uint8_t> export_plan(const Plan& plan) {
     }
     emit_node(plan.nodes, 0, o);
     return o;
+}
+
+namespace {
+
+// Bounds-checked little-endian reader over an export image.
+struct Reader {
+    const uint8_t* p;
+    size_t left;
+    template <typename T>
+    bool get(T& v) {
+        if (left < sizeof(T)) return false;
+        std::memcpy(&v, p, sizeof(T));
+        p += sizeof(T);
+        left -= sizeof(T);
+        return true;
+    }
+};
+
+}  // namespace
+
+bool import_plan(const void* buf, size_t size, int32_t n, Plan& out, std::string& why) {
+    out = Plan();
+    Reader rd{static_cast<const uint8_t*>(buf), size};
+    int32_t h[12];
+    for (int32_t& v : h)
+        if (!rd.get(v)) return why = "image shorter than its header", false;
+    if (h[0] != 0x45434152 || h[1] != 1) return why = "not a schedule image (magic or version)", false;
+    if (h[2] != n) return why = "image was built for another number of rows", false;
+    const int32_t n_nodes = h[7], n_phases = h[8], n_leaves = h[9];
+    if (h[3] < 1 || h[4] != 2 || (h[5] != RACE_BAL_ROWS && h[5] != RACE_BAL_NNZ) || h[6] < -1 || n_nodes < 1 ||
+        n_phases < 0 || n_leaves < 0 || h[10] != 0 || h[11] != 0)
+        return why = "header field out of range", false;
+    // the remaining size is fixed by the header's counts
+    const uint64_t want = 8ull * 9 + 4ull * static_cast<uint64_t>(n) + 4ull * (static_cast<uint64_t>(n_phases) + 1) +
+                          8ull * static_cast<uint64_t>(n_leaves) + static_cast<uint64_t>(n_nodes) * (11 * 4 + 2 * 8);
+    if (rd.left != want) return why = "image size does not match its header", false;
+    out.n = n;
+    out.n_workers = h[3];
+    out.dist_k = h[4];
+    out.balance = h[5];
+    out.max_depth = h[6];
+    for (double& e : out.eps) rd.get(e);
+    rd.get(out.eta);
+    for (double e : out.eps)
+        if (!(e >= 0.5 && e < 1.0)) return why = "eps_s outside [0.5, 1)", false;
+    out.perm.resize(static_cast<size_t>(n));
+    std::vector<uint8_t> hit(static_cast<size_t>(n), 0);
+    for (int32_t& v : out.perm) {
+        rd.get(v);
+        if (v < 0 || v >= n || hit[static_cast<size_t>(v)]) return why = "perm is not a permutation", false;
+        hit[static_cast<size_t>(v)] = 1;
+    }
+    out.stage_ptr.resize(static_cast<size_t>(n_phases) + 1);
+    for (int32_t& v : out.stage_ptr) rd.get(v);
+    if (out.stage_ptr.front() != 0 || out.stage_ptr.back() != n_leaves)
+        return why = "phase offsets do not span the leaves", false;
+    for (size_t q = 1; q < out.stage_ptr.size(); ++q)
+        if (out.stage_ptr[q] < out.stage_ptr[q - 1]) return why = "phase offsets decrease", false;
+    out.leaf_lo.resize(static_cast<size_t>(n_leaves));
+    out.leaf_hi.resize(static_cast<size_t>(n_leaves));
+    std::fill(hit.begin(), hit.end(), 0);
+    for (int32_t q = 0; q < n_leaves; ++q) {
+        int32_t lo, hi;
+        rd.get(lo);
+        rd.get(hi);
+        if (lo < 0 || lo >= hi || hi > n) return why = "leaf row range out of bounds or empty", false;
+        for (int32_t r = lo; r < hi; ++r) {
+            if (hit[static_cast<size_t>(r)]) return why = "a row belongs to two leaves", false;
+            hit[static_cast<size_t>(r)] = 1;
+        }
+        out.leaf_lo[static_cast<size_t>(q)] = lo;
+        out.leaf_hi[static_cast<size_t>(q)] = hi;
+    }
+    for (uint8_t v : hit)
+        if (!v) return why = "a row belongs to no leaf", false;
+    // the tree in preorder; an explicit stack of (node, children still to read)
+    out.nodes.resize(static_cast<size_t>(n_nodes));
+    std::vector<std::pair<int32_t, int32_t>> open;
+    for (int32_t id = 0; id < n_nodes; ++id) {
+        if (id > 0 && open.empty()) return why = "tree has more than one root", false;
+        TreeNode& t = out.nodes[static_cast<size_t>(id)];
+        int32_t kids = 0;
+        for (int32_t* f : {&t.stage, &t.color, &t.lo, &t.hi, &t.n_threads, &t.thread_lo, &t.n_levels, &t.n_sub, &kids,
+                           &t.phase_count, &t.phase_off})
+            rd.get(*f);
+        rd.get(t.size);
+        rd.get(t.neff);
+        if (t.lo < 0 || t.lo > t.hi || t.hi > n || kids < 0 || kids > n_nodes - 1 - id || t.stage < -1 ||
+            (t.color != 0 && t.color != 1) || t.n_threads < 1)
+            return why = "tree node field out of range", false;
+        if (!open.empty()) {
+            out.nodes[static_cast<size_t>(open.back().first)].kids.push_back(id);
+            if (--open.back().second == 0) open.pop_back();
+        }
+        if (kids > 0) open.emplace_back(id, kids);
+    }
+    if (!open.empty()) return why = "tree ends before its last child", false;
+    out.n_levels = out.nodes[0].n_sub;
+    return true;
 }
 
 }  // namespace race

@@ -263,6 +263,68 @@ static int upload_schedule(race_schedule* s, cudaStream_t st) {
     return rc;
 }
 
+// Matrix checks shared by race_build and race_import (the rest is checked
+// entry by entry by canonicalize).
+static int check_matrix(const race_csr_upper* a) {
+    if (a->n <= 0) return fail(RACE_ERR_INVALID, "n <= 0");
+    if (a->nnz < 0 || (a->nnz > 0 && (!a->col || !a->val)) || !a->row_ptr) return fail(RACE_ERR_INVALID, "NULL matrix array");
+    if (a->nnz + a->n >= static_cast<int64_t>(INT32_MAX)) return fail(RACE_ERR_OVERFLOW, "nnz + n >= 2^31");
+    if (a->val_type != RACE_F64 && a->val_type != RACE_F32) return fail(RACE_ERR_INVALID, "val_type");
+    return RACE_OK;
+}
+
+// True when no two leaves of one phase update the same entry of b: a leaf's
+// rows write b at their own index and at every stored column (Alg.
+// "SymmSpMV"), so the write sets of concurrent leaves must be disjoint
+// (the distance-2 condition of Sec. 4.2).
+static bool phases_conflict_free(const race::Plan& plan, const std::vector<int32_t>& rp, const std::vector<int32_t>& col) {
+    std::vector<int32_t> phase_of(static_cast<size_t>(plan.n), -1), leaf_of(static_cast<size_t>(plan.n), -1);
+    for (size_t ph = 0; ph + 1 < plan.stage_ptr.size(); ++ph)
+        for (int32_t q = plan.stage_ptr[ph]; q < plan.stage_ptr[ph + 1]; ++q)
+            for (int32_t r = plan.leaf_lo[static_cast<size_t>(q)]; r < plan.leaf_hi[static_cast<size_t>(q)]; ++r)
+                for (int32_t t = rp[static_cast<size_t>(r)]; t < rp[static_cast<size_t>(r) + 1]; ++t) {
+                    const size_t c = static_cast<size_t>(col[static_cast<size_t>(t)]);
+                    if (phase_of[c] == static_cast<int32_t>(ph) && leaf_of[c] != q) return false;
+                    phase_of[c] = static_cast<int32_t>(ph);
+                    leaf_of[c] = q;
+                }
+    return true;
+}
+
+// Common tail of race_build and race_import: value storage, launch
+// defaults and (unless host-only) the device upload.
+static int finish_schedule(race_schedule* s, int32_t val_type, int32_t group_lanes, uint32_t flags, void* stream,
+                           race_schedule** out) {
+    try {
+        s->val_type = val_type;
+        if (val_type == RACE_F32) {
+            s->h_val32.assign(s->h_val64.begin(), s->h_val64.end());
+            std::vector<double>().swap(s->h_val64);
+        }
+    } catch (const std::bad_alloc&) {
+        delete s;
+        return fail(RACE_ERR_NOMEM, "host allocation during build");
+    }
+    s->group_lanes = group_lanes ? group_lanes : pick_lanes(static_cast<int64_t>(s->h_col.size()), s->plan.n);
+    s->launch.executor = RACE_EXEC_LEAF_GROUP;
+    s->launch.group_lanes = s->group_lanes;
+    s->launch.rows_per_group = 4;
+    s->launch.blocks_per_sm = 0;
+    s->launch.regs_per_row = 8;
+    s->host_only = (flags & RACE_FLAG_HOST_ONLY) ? 1 : 0;
+    s->want_windows = (flags & RACE_FLAG_NO_WINDOWS) ? 0 : 1;
+    if (!s->host_only) {
+        const int rc = upload_schedule(s, static_cast<cudaStream_t>(stream));
+        if (rc != RACE_OK) {
+            release_device(s);
+            delete s;
+            return rc;
+        }
+    }
+    *out = s;
+    return RACE_OK;
+}
+
 extern "C" {
 
 void race_default_params(race_params* p, int32_t n_workers) {
@@ -283,10 +345,8 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
     if (!out) return fail(RACE_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (!a || !p) return fail(RACE_ERR_INVALID, "NULL argument");
-    if (a->n <= 0) return fail(RACE_ERR_INVALID, "n <= 0");
-    if (a->nnz < 0 || (a->nnz > 0 && (!a->col || !a->val)) || !a->row_ptr) return fail(RACE_ERR_INVALID, "NULL matrix array");
-    if (a->nnz + a->n >= static_cast<int64_t>(INT32_MAX)) return fail(RACE_ERR_OVERFLOW, "nnz + n >= 2^31");
-    if (a->val_type != RACE_F64 && a->val_type != RACE_F32) return fail(RACE_ERR_INVALID, "val_type");
+    int rc = check_matrix(a);
+    if (rc != RACE_OK) return rc;
     if (p->dist_k != 2) return fail(RACE_ERR_UNSUPPORTED, "only distance-2 colouring (SymmSpMV) is built");
     if (p->n_workers < 1) return fail(RACE_ERR_INVALID, "n_workers < 1");
     for (int i = 0; i < 8; ++i)
@@ -294,10 +354,11 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
     if (p->balance != RACE_BAL_ROWS && p->balance != RACE_BAL_NNZ) return fail(RACE_ERR_INVALID, "balance");
     if (p->group_lanes != 0 && p->group_lanes != 4 && p->group_lanes != 8 && p->group_lanes != 16 && p->group_lanes != 32)
         return fail(RACE_ERR_INVALID, "group_lanes must be 0, 4, 8, 16 or 32");
+    if ((p->flags & RACE_FLAG_PSEUDO_PERIPHERAL) && (p->flags & RACE_FLAG_NATURAL_ORDER))
+        return fail(RACE_ERR_INVALID, "RACE_FLAG_PSEUDO_PERIPHERAL has no effect with RACE_FLAG_NATURAL_ORDER");
 
     race_schedule* s = new (std::nothrow) race_schedule();
     if (!s) return fail(RACE_ERR_NOMEM, "host allocation");
-    int rc = RACE_OK;
     try {
         std::vector<int32_t> rp, col;
         std::vector<double> val;
@@ -309,33 +370,48 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
         if (p->flags & RACE_FLAG_NATURAL_ORDER) race::natural_plan(a->n, *p, s->plan);
         else race::build_plan(a->n, rp.data(), col.data(), *p, s->plan);
         permute_upper(a->n, rp, col, val, s->plan.perm, s->h_rp, s->h_col, s->h_val64);
-        s->val_type = a->val_type;
-        if (a->val_type == RACE_F32) {
-            s->h_val32.assign(s->h_val64.begin(), s->h_val64.end());
-            std::vector<double>().swap(s->h_val64);
-        }
-        s->group_lanes = p->group_lanes ? p->group_lanes : pick_lanes(static_cast<int64_t>(s->h_col.size()), a->n);
-        s->launch.executor = RACE_EXEC_LEAF_GROUP;
-        s->launch.group_lanes = s->group_lanes;
-        s->launch.rows_per_group = 4;
-        s->launch.blocks_per_sm = 0;
-        s->launch.regs_per_row = 8;
-        s->host_only = (p->flags & RACE_FLAG_HOST_ONLY) ? 1 : 0;
     } catch (const std::bad_alloc&) {
         delete s;
         return fail(RACE_ERR_NOMEM, "host allocation during build");
     }
-    s->want_windows = (p->flags & RACE_FLAG_NO_WINDOWS) ? 0 : 1;
-    if (!s->host_only) {
-        rc = upload_schedule(s, static_cast<cudaStream_t>(stream));
+    return finish_schedule(s, a->val_type, p->group_lanes, p->flags, stream, out);
+}
+
+int race_import(const race_csr_upper* a, const void* image, size_t size, uint32_t flags, void* stream,
+                race_schedule** out) {
+    if (!out) return fail(RACE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!a || !image) return fail(RACE_ERR_INVALID, "NULL argument");
+    if (flags & ~(RACE_FLAG_HOST_ONLY | RACE_FLAG_NO_WINDOWS))
+        return fail(RACE_ERR_INVALID, "race_import takes only RACE_FLAG_HOST_ONLY and RACE_FLAG_NO_WINDOWS");
+    int rc = check_matrix(a);
+    if (rc != RACE_OK) return rc;
+    race_schedule* s = new (std::nothrow) race_schedule();
+    if (!s) return fail(RACE_ERR_NOMEM, "host allocation");
+    try {
+        std::vector<int32_t> rp, col;
+        std::vector<double> val;
+        rc = canonicalize(a, rp, col, val);
         if (rc != RACE_OK) {
-            release_device(s);
             delete s;
             return rc;
         }
+        std::string why;
+        if (!race::import_plan(image, size, a->n, s->plan, why)) {
+            delete s;
+            return fail(RACE_ERR_INVALID, "schedule image: " + why);
+        }
+        permute_upper(a->n, rp, col, val, s->plan.perm, s->h_rp, s->h_col, s->h_val64);
+        if (!phases_conflict_free(s->plan, s->h_rp, s->h_col)) {
+            delete s;
+            return fail(RACE_ERR_INVALID, "schedule image: two leaves of one phase update the same entry of b "
+                                          "(not a distance-2 colouring of this matrix)");
+        }
+    } catch (const std::bad_alloc&) {
+        delete s;
+        return fail(RACE_ERR_NOMEM, "host allocation during import");
     }
-    *out = s;
-    return RACE_OK;
+    return finish_schedule(s, a->val_type, 0, flags, stream, out);
 }
 
 int race_upload(race_schedule* s, void* stream) {

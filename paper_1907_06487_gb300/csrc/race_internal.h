@@ -49,6 +49,11 @@ void natural_plan(int32_t n, const race_params& p, Plan& out);
 // Canonical export image (layout documented in race.h).
 std::vector<uint8_t> export_plan(const Plan& plan);
 
+// Inverse of export_plan for a matrix of n rows: every field is checked
+// (sizes, permutation, phase offsets, leaves covering each row exactly
+// once, the tree's shape); false with the reason in `why` on any mismatch.
+bool import_plan(const void* buf, size_t size, int32_t n, Plan& out, std::string& why);
+
 }  // namespace race
 
 // Capacities of the shared-memory windows of the window executors: write
