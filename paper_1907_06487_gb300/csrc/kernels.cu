@@ -508,6 +508,81 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
     }
 }
 
+// How a row of the double-float SymmSpMM forms its transposed products:
+// split (double-float), FP64 multiplies, or none (x_r is zero).
+enum MmScatter { kMmSplit = 0, kMmFp64 = 1, kMmNone = 2 };
+
+// One row of k_symm_mm_rows_df for the lane of right-hand side c: the FP64
+// row sum is returned, the transposed updates go to B as reductions.  The
+// mode is fixed for the whole row, so the entry loop carries no per-entry
+// mode branches (3-9 % faster than choosing per entry).
+template <typename VT, int K, int MODE>
+__device__ __forceinline__ double mm_row_df(int32_t js, int32_t je, int c, const int32_t* __restrict__ col,
+                                            const VT* __restrict__ val, const double* __restrict__ X, double* B,
+                                            double xr, float xrh, float xrl) {
+    double acc = 0.0;
+    constexpr int U = 4;
+    for (int32_t p = js; p < je; p += U) {
+        VT araw[U];
+        double xc[U];
+        int32_t cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool v = p + u < je;
+            araw[u] = v ? __ldg(val + p + u) : VT(0);
+            cc[u] = v ? __ldg(col + p + u) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xc[u] = cc[u] >= 0 ? __ldg(X + static_cast<int64_t>(cc[u]) * K + c) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (cc[u] < 0) continue;
+            const double a = df64::widen(araw[u]);
+            acc = fma(a, xc[u], acc);
+            if (p + u == js) continue;  // the diagonal (first entry) has no transposed update
+            if constexpr (MODE == kMmSplit) {
+                if (!df64::is_zero(araw[u])) {
+                    float ah, al, ph, pl;
+                    df64::split_value(araw[u], ah, al);
+                    df64::mul(ah, al, xrh, xrl, ph, pl);
+                    atomicAdd(B + static_cast<int64_t>(cc[u]) * K + c, df64::join(ph, pl));
+                }
+            } else if constexpr (MODE == kMmFp64) {
+                atomicAdd(B + static_cast<int64_t>(cc[u]) * K + c, a * xr);
+            }
+        }
+    }
+    return acc;
+}
+
+// SymmSpMM with double-float transposed products, one row per group of K
+// lanes (lane c owns right-hand side c) and rows strided over the grid.  The
+// lane's mode for the row: x_r outside the split's range or a warp of the
+// FP64 share (warp-uniform, the first fp64_quarters of every four warps):
+// FP64 multiplies; x_r zero: no transposed updates; else double-float.
+template <typename VT, int K>
+__global__ void __launch_bounds__(kBlock) k_symm_mm_rows_df(int32_t n, const int32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ col,
+                                                           const VT* __restrict__ val, const double* __restrict__ X,
+                                                           double* B, int fp64_quarters) {
+    const int c = threadIdx.x & (K - 1);
+    const bool warp64 = ((static_cast<int>(blockIdx.x) * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5)) & 3) <
+                        fp64_quarters;
+    const int64_t grp = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / K;
+    const int64_t ngrp = static_cast<int64_t>(gridDim.x) * kBlock / K;
+    for (int64_t r = grp; r < n; r += ngrp) {
+        const int32_t js = __ldg(rp + r), je = __ldg(rp + r + 1);
+        const double xr = __ldg(X + r * K + c);
+        float xrh, xrl;
+        const int st = df64::split(xr, xrh, xrl);
+        double acc;
+        if (st != 0 || warp64) acc = mm_row_df<VT, K, kMmFp64>(js, je, c, col, val, X, B, xr, xrh, xrl);
+        else if (xrh == 0.0f) acc = mm_row_df<VT, K, kMmNone>(js, je, c, col, val, X, B, xr, xrh, xrl);
+        else acc = mm_row_df<VT, K, kMmSplit>(js, je, c, col, val, X, B, xr, xrh, xrl);
+        atomicAdd(B + r * K + c, acc);
+    }
+}
+
 // Diagnostics of race_probe_scatter, shaped like the row-parallel executors
 // (one row per thread, four entries per step): mode 0 replays the transposed
 // update's reductions with a constant value, mode 1 streams the column
@@ -725,6 +800,7 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
         const int g = grid_for((static_cast<int64_t>(n) * KK + R - 1) / R, s->launch.blocks_per_sm);              \
         if (R == 4) k_symm_mm_rows_red<VT, KK, 4, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);        \
         else if (R == 2) k_symm_mm_rows_red<VT, KK, 2, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);   \
+        else if (DFV) k_symm_mm_rows_df<VT, KK><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);               \
         else k_symm_mm_rows_red<VT, KK, 1, DFV><<<g, kBlock, 0, st>>>(n, s->d_rp, s->d_col, v, X, B, q64);               \
     } while (0)
 #define RACE_MM_ROWS(KK)                 \
