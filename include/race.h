@@ -78,6 +78,19 @@ extern "C" {
                                    vertex (Sec. 6.1); this flag gives other
                                    orders the same start.  Recursion roots
                                    are unchanged.                           */
+#define RACE_FLAG_RCM 16u /* relabel the matrix by reverse Cuthill-McKee
+                                   before the construction, as the paper does
+                                   with all of its inputs (Sec. 6.1): each
+                                   component (in the order of its lowest
+                                   vertex) from its pseudo-peripheral vertex,
+                                   breadth first, the neighbours newly reached
+                                   from a vertex by increasing degree (lowest
+                                   index on ties), the sequence reversed.  The
+                                   RACE levels then keep the RCM order inside
+                                   each level; the schedule's permutation is
+                                   composed with it.  With
+                                   RACE_FLAG_NATURAL_ORDER: the RCM order
+                                   alone, one leaf.                         */
 
 /* Upper-triangle CRS matrix in HOST memory (Sec. 3.2, Alg. "SymmSpMV"):
  * row i holds the entries (i, j) with j >= i.  Columns may come in any

@@ -89,6 +89,8 @@ def _get():
     L.orc_bfs_dist.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, _i32p]
     L.orc_pseudo_peripheral.restype = ctypes.c_int32
     L.orc_pseudo_peripheral.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32]
+    L.orc_rcm_order.restype = ctypes.c_int32
+    L.orc_rcm_order.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
     _lib = L
     return L
 
@@ -219,17 +221,25 @@ def pseudo_peripheral(m, start):
     return int(_get().orc_pseudo_peripheral(n, _p(rp, _i32p), _p(ci, _i32p), int(start)))
 
 
+def rcm_order(m):
+    """Reverse Cuthill-McKee order, order[new] = old."""
+    n, rp, ci, _ = _mat(m)
+    out = np.zeros(n, np.int32)
+    _get().orc_rcm_order(n, _p(rp, _i32p), _p(ci, _i32p), _p(out, _i32p))
+    return out
+
+
 class Race:
     """The oracle's RACE schedule for one matrix (Sec. 4-5 of the paper)."""
 
-    def __init__(self, m, n_workers, eps=DEFAULT_EPS, max_depth=-1, balance=0, pseudo_peripheral=False):
+    def __init__(self, m, n_workers, eps=DEFAULT_EPS, max_depth=-1, balance=0, pseudo_peripheral=False, rcm=False):
         n, rp, ci, _ = _mat(m)
         e = np.zeros(8)
         e[:len(eps)] = eps
         if len(eps) < 8:
             e[len(eps):] = eps[-1]
         self._h = _get().orc_race(n, _p(rp, _i32p), _p(ci, _i32p), int(n_workers), _p(e, _f64p),
-                                  int(max_depth), int(balance), int(bool(pseudo_peripheral)))
+                                  int(max_depth), int(balance), int(bool(pseudo_peripheral)) | (2 if rcm else 0))
         if not self._h:
             raise ValueError("oracle race build failed")
         info = np.zeros(6, np.int32)

@@ -39,6 +39,11 @@
  *      roots become a pseudo-peripheral vertex of their component
  *      (George and Liu, ACM TOMS 5, 1979), the start node of the RCM
  *      orderings the paper's inputs carry (Sec. 6.1).
+ *   Opt-in RCM: the construction runs on the matrix relabelled by reverse
+ *      Cuthill-McKee (components in the order of their lowest vertex, each
+ *      from its pseudo-peripheral vertex; neighbours newly reached from a
+ *      vertex taken by increasing degree, lowest index on ties; the whole
+ *      sequence reversed), and its permutation is composed with that order.
  *   R2 BFS runs until the frontier is empty; unvisited vertices of the group
  *      restart from the last unvisited one at (max level so far) + 2
  *      (islands, Sec. 4.4.1).
@@ -363,6 +368,39 @@ static int32_t pseudo_peripheral(int32_t n, const int64_t *aptr, const int32_t *
     return r;
 }
 
+/* Reverse Cuthill-McKee sequence (out[new] = old) of the graph aptr/adj.   */
+static void rcm_sequence(int32_t n, const int64_t *aptr, const int32_t *adj, int32_t *out) {
+    char *seen = (char *)calloc((size_t)n, 1);
+    int32_t *kids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t len = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        if (seen[v]) continue;
+        int32_t head = len;
+        int32_t start = pseudo_peripheral(n, aptr, adj, v);
+        out[len++] = start; seen[start] = 1;
+        while (head < len) {
+            int32_t u = out[head++], nk = 0;
+            for (int64_t e = aptr[u]; e < aptr[u + 1]; ++e)
+                if (!seen[adj[e]]) { seen[adj[e]] = 1; kids[nk++] = adj[e]; }
+            /* insertion sort by (degree, index) */
+            for (int32_t i = 1; i < nk; ++i) {
+                int32_t w = kids[i], j = i;
+                int64_t dw = aptr[w + 1] - aptr[w];
+                while (j > 0) {
+                    int32_t z = kids[j - 1];
+                    int64_t dz = aptr[z + 1] - aptr[z];
+                    if (dz < dw || (dz == dw && z < w)) break;
+                    kids[j] = z; --j;
+                }
+                kids[j] = w;
+            }
+            for (int32_t i = 0; i < nk; ++i) out[len++] = kids[i];
+        }
+    }
+    for (int32_t i = 0, j = n - 1; i < j; ++i, --j) { int32_t t = out[i]; out[i] = out[j]; out[j] = t; }
+    free(kids); free(seen);
+}
+
 /* Level construction on the group order[lo..hi) (Alg. "Construction of
  * levels", Eq. "level"), restricted to the group plus its distance-1 halo
  * unless whole_graph.  Rewrites order[lo..hi) level by level (R3) and
@@ -638,12 +676,36 @@ static int cmp_leaf(const void *a, const void *b) {
 
 void orc_race_free(osched *S);
 
+int orc_permute_upper(int32_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                      const int32_t *perm, int32_t *orp, int32_t *oci, double *ova);
+int32_t orc_rcm_order(int32_t n, const int32_t *rp, const int32_t *ci, int32_t *order);
+
+/* options: bit 0 = pseudo-peripheral stage-0 roots, bit 1 = RCM relabelling
+ * first (see the readings above).                                         */
 osched *orc_race(int32_t n, const int32_t *rp, const int32_t *ci, int32_t nt, const double *eps8,
-                 int32_t max_depth, int32_t balance, int32_t pseudo_peripheral_root) {
+                 int32_t max_depth, int32_t balance, int32_t options) {
     if (n <= 0 || nt <= 0) return NULL;
+    if (options & 2) {
+        /* build on the RCM-relabelled matrix, then compose the permutations */
+        int64_t nnz = rp[n];
+        int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        int32_t *prp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+        int32_t *pci = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+        double *zero = (double *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+        double *pva = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+        orc_rcm_order(n, rp, ci, ord);
+        orc_permute_upper(n, rp, ci, zero, ord, prp, pci, pva);
+        osched *S = orc_race(n, prp, pci, nt, eps8, max_depth, balance, options & ~2);
+        if (S) {
+            for (int32_t i = 0; i < n; ++i) S->order[i] = ord[S->order[i]];
+            for (int32_t i = 0; i < n; ++i) S->pos[S->order[i]] = i;
+        }
+        free(ord); free(prp); free(pci); free(zero); free(pva);
+        return S;
+    }
     osched *S = (osched *)calloc(1, sizeof(osched));
     S->n = n; S->nt = nt; S->k = 2; S->balance = balance; S->max_depth = max_depth;
-    S->pp = pseudo_peripheral_root != 0;
+    S->pp = (options & 1) != 0;
     for (int i = 0; i < 8; ++i) S->eps[i] = eps8[i];
     /* symmetric adjacency (self loops dropped, Sec. 4 graph definitions) */
     S->aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -855,6 +917,25 @@ int32_t orc_pseudo_peripheral(int32_t n, const int32_t *rp, const int32_t *ci, i
     int32_t r = pseudo_peripheral(n, aptr, adj, start);
     free(fill); free(adj); free(aptr);
     return r;
+}
+
+/* Reverse Cuthill-McKee order (order[new] = old) of the symmetric graph of
+ * an upper CRS; returns n.                                                 */
+int32_t orc_rcm_order(int32_t n, const int32_t *rp, const int32_t *ci, int32_t *order) {
+    int64_t *aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { aptr[i + 1]++; aptr[ci[t] + 1]++; }
+    for (int32_t i = 0; i < n; ++i) aptr[i + 1] += aptr[i];
+    int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(aptr[n] > 0 ? aptr[n] : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    memcpy(fill, aptr, sizeof(int64_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t)
+            if (ci[t] != i) { adj[fill[i]++] = ci[t]; adj[fill[ci[t]]++] = i; }
+    rcm_sequence(n, aptr, adj, order);
+    free(fill); free(adj); free(aptr);
+    return n;
 }
 
 /* Plain BFS distances on the whole graph from one root (Eq. "level").    */

@@ -37,6 +37,7 @@ RACE_FLAG_HOST_ONLY = 1
 RACE_FLAG_NO_WINDOWS = 2
 RACE_FLAG_NATURAL_ORDER = 4
 RACE_FLAG_PSEUDO_PERIPHERAL = 8
+RACE_FLAG_RCM = 16
 
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
@@ -206,7 +207,7 @@ def _check(rc, where):
 
 
 def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False,
-                windows=True, natural_order=False, pseudo_peripheral=False):
+                windows=True, natural_order=False, pseudo_peripheral=False, rcm=False):
     p = race_params()
     lib().race_default_params(ctypes.byref(p), int(n_workers))
     e = list(eps) + [eps[-1]] * (8 - len(eps))
@@ -217,7 +218,7 @@ def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, g
     p.group_lanes = int(group_lanes)
     p.flags = ((RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
                | (RACE_FLAG_NATURAL_ORDER if natural_order else 0)
-               | (RACE_FLAG_PSEUDO_PERIPHERAL if pseudo_peripheral else 0))
+               | (RACE_FLAG_PSEUDO_PERIPHERAL if pseudo_peripheral else 0) | (RACE_FLAG_RCM if rcm else 0))
     return p
 
 
@@ -294,11 +295,11 @@ def _csr(m, val_type):
 
 def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
                host_only=False, stream=None, val_type=RACE_F64, windows=True, natural_order=False,
-               pseudo_peripheral=False) -> Schedule:
+               pseudo_peripheral=False, rcm=False) -> Schedule:
     """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
     a, keep = _csr(m, val_type)
     p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows, natural_order,
-                    pseudo_peripheral)
+                    pseudo_peripheral, rcm)
     h = ctypes.c_void_p()
     _check(lib().race_build(ctypes.byref(a), ctypes.byref(p), _stream(stream), ctypes.byref(h)), "race_build")
     del keep

@@ -72,6 +72,63 @@ Graph make_graph(int32_t n, const int32_t* rp, const int32_t* col) {
     return g;
 }
 
+// George and Liu's pseudo-peripheral vertex of v's connected component
+// (ACM TOMS 5, 1979): from the current start, take a vertex of minimum
+// degree (lowest index on ties) among those farthest away; move there while
+// its eccentricity is larger, stop at the first start that is not beaten.
+class PeripheralFinder {
+public:
+    explicit PeripheralFinder(const Graph& g) : g_(g) {}
+
+    int32_t find(int32_t v) {
+        std::vector<int32_t> far, far_u;
+        int32_t ecc = eccentricity(v, far);
+        for (;;) {
+            int32_t u = far[0];
+            for (int32_t w : far) {
+                const int64_t dw = degree(w), du = degree(u);
+                if (dw < du || (dw == du && w < u)) u = w;
+            }
+            const int32_t ecc_u = eccentricity(u, far_u);
+            if (ecc_u <= ecc) return v;
+            v = u;
+            ecc = ecc_u;
+            far.swap(far_u);
+        }
+    }
+
+    int64_t degree(int32_t v) const { return g_.off[v + 1] - g_.off[v]; }
+
+private:
+    // Eccentricity of v; `far` receives the vertices at that distance.
+    int32_t eccentricity(int32_t v, std::vector<int32_t>& far) {
+        if (mark_.empty()) mark_.assign(g_.off.size() - 1, 0);
+        const uint32_t s = ++stamp_;
+        std::vector<int32_t> front(1, v), next;
+        mark_[static_cast<size_t>(v)] = s;
+        int32_t ecc = 0;
+        for (;;) {
+            next.clear();
+            for (int32_t u : front)
+                for (int64_t e = g_.off[u]; e < g_.off[u + 1]; ++e) {
+                    const int32_t w = g_.nbr[e];
+                    if (mark_[static_cast<size_t>(w)] == s) continue;
+                    mark_[static_cast<size_t>(w)] = s;
+                    next.push_back(w);
+                }
+            if (next.empty()) break;
+            front.swap(next);
+            ++ecc;
+        }
+        far.swap(front);
+        return ecc;
+    }
+
+    const Graph& g_;
+    std::vector<uint32_t> mark_;
+    uint32_t stamp_ = 0;
+};
+
 struct LevelSet {
     int32_t count = 0;
     std::vector<int64_t> weight;  // balancing unit per level
@@ -143,7 +200,7 @@ private:
         std::vector<int32_t> front, next;
         while (left > 0) {
             do { --cursor; } while (seen_[seq_[cursor]] == s);
-            const int32_t root = (whole && (p_.flags & RACE_FLAG_PSEUDO_PERIPHERAL)) ? pseudo_peripheral(seq_[cursor])
+            const int32_t root = (whole && (p_.flags & RACE_FLAG_PSEUDO_PERIPHERAL)) ? pp_.find(seq_[cursor])
                                                                                      : seq_[cursor];
             int32_t lev = top < 0 ? 0 : top + 2;
             seen_[root] = s;
@@ -188,52 +245,6 @@ private:
         }
         std::copy(scratch_.begin(), scratch_.end(), seq_.begin() + lo);
         return ls;
-    }
-
-    // Eccentricity of v in the whole graph; `far` receives the vertices at
-    // that distance (in BFS order).
-    int32_t eccentricity(int32_t v, std::vector<int32_t>& far) {
-        if (pp_mark_.empty()) pp_mark_.assign(static_cast<size_t>(n_), 0);
-        const uint32_t s = ++pp_stamp_;
-        std::vector<int32_t> front(1, v), next;
-        pp_mark_[static_cast<size_t>(v)] = s;
-        int32_t ecc = 0;
-        for (;;) {
-            next.clear();
-            for (int32_t u : front)
-                for (int64_t e = g_.off[u]; e < g_.off[u + 1]; ++e) {
-                    const int32_t w = g_.nbr[e];
-                    if (pp_mark_[static_cast<size_t>(w)] == s) continue;
-                    pp_mark_[static_cast<size_t>(w)] = s;
-                    next.push_back(w);
-                }
-            if (next.empty()) break;
-            front.swap(next);
-            ++ecc;
-        }
-        far.swap(front);
-        return ecc;
-    }
-
-    // George and Liu's pseudo-peripheral vertex of v's connected component:
-    // from the current start, take a vertex of minimum degree (lowest index
-    // on ties) among those farthest away; move there while its eccentricity
-    // is larger, stop at the first start that is not beaten.
-    int32_t pseudo_peripheral(int32_t v) {
-        std::vector<int32_t> far, far_u;
-        int32_t ecc = eccentricity(v, far);
-        for (;;) {
-            int32_t u = far[0];
-            for (int32_t w : far) {
-                const int64_t dw = g_.off[w + 1] - g_.off[w], du = g_.off[u + 1] - g_.off[u];
-                if (dw < du || (dw == du && w < u)) u = w;
-            }
-            const int32_t ecc_u = eccentricity(u, far_u);
-            if (ecc_u <= ecc) return v;
-            v = u;
-            ecc = ecc_u;
-            far.swap(far_u);
-        }
     }
 
     struct Pair {
@@ -467,8 +478,7 @@ private:
     std::vector<int32_t> depth_of_;
     std::vector<int32_t> scratch_;
     uint32_t stamp_ = 0;
-    std::vector<uint32_t> pp_mark_;  // BFS stamps of the pseudo-peripheral search
-    uint32_t pp_stamp_ = 0;
+    PeripheralFinder pp_{g_};
 };
 
 template <typename T>
@@ -500,6 +510,42 @@ void build_plan(int32_t n, const int32_t* row_ptr, const int32_t* col, const rac
     for (int i = 0; i < 8; ++i) out.eps[i] = p.eps[i];
     Builder b(n, row_ptr, col, p, out);
     b.run();
+}
+
+std::vector<int32_t> rcm_order(int32_t n, const int32_t* row_ptr, const int32_t* col) {
+    const Graph g = make_graph(n, row_ptr, col);
+    PeripheralFinder pf(g);
+    std::vector<int32_t> cm;
+    cm.reserve(static_cast<size_t>(n));
+    std::vector<uint8_t> seen(static_cast<size_t>(n), 0);
+    std::vector<int32_t> kids;
+    for (int32_t v = 0; v < n; ++v) {
+        if (seen[static_cast<size_t>(v)]) continue;
+        // Cuthill-McKee from a pseudo-peripheral vertex of v's component:
+        // breadth first, each vertex's newly reached neighbours appended by
+        // increasing degree (lowest index on ties)
+        const int32_t start = pf.find(v);
+        size_t head = cm.size();
+        cm.push_back(start);
+        seen[static_cast<size_t>(start)] = 1;
+        while (head < cm.size()) {
+            const int32_t u = cm[head++];
+            kids.clear();
+            for (int64_t e = g.off[u]; e < g.off[u + 1]; ++e) {
+                const int32_t w = g.nbr[e];
+                if (seen[static_cast<size_t>(w)]) continue;
+                seen[static_cast<size_t>(w)] = 1;
+                kids.push_back(w);
+            }
+            std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) {
+                const int64_t da = pf.degree(a), db = pf.degree(b);
+                return da < db || (da == db && a < b);
+            });
+            cm.insert(cm.end(), kids.begin(), kids.end());
+        }
+    }
+    std::reverse(cm.begin(), cm.end());
+    return cm;
 }
 
 void natural_plan(int32_t n, const race_params& p, Plan& out) {

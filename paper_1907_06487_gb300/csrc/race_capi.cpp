@@ -356,6 +356,9 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
         return fail(RACE_ERR_INVALID, "group_lanes must be 0, 4, 8, 16 or 32");
     if ((p->flags & RACE_FLAG_PSEUDO_PERIPHERAL) && (p->flags & RACE_FLAG_NATURAL_ORDER))
         return fail(RACE_ERR_INVALID, "RACE_FLAG_PSEUDO_PERIPHERAL has no effect with RACE_FLAG_NATURAL_ORDER");
+    if (p->flags & ~(RACE_FLAG_HOST_ONLY | RACE_FLAG_NO_WINDOWS | RACE_FLAG_NATURAL_ORDER | RACE_FLAG_PSEUDO_PERIPHERAL |
+                     RACE_FLAG_RCM))
+        return fail(RACE_ERR_INVALID, "unknown flag bits");
 
     race_schedule* s = new (std::nothrow) race_schedule();
     if (!s) return fail(RACE_ERR_NOMEM, "host allocation");
@@ -367,8 +370,21 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
             delete s;
             return rc;
         }
-        if (p->flags & RACE_FLAG_NATURAL_ORDER) race::natural_plan(a->n, *p, s->plan);
-        else race::build_plan(a->n, rp.data(), col.data(), *p, s->plan);
+        if (p->flags & RACE_FLAG_RCM) {
+            // the construction runs on the RCM-ordered matrix; its permutation
+            // is then composed with the RCM order (new -> RCM label -> input)
+            const std::vector<int32_t> order = race::rcm_order(a->n, rp.data(), col.data());
+            std::vector<int32_t> rp1, col1;
+            std::vector<double> val1;
+            permute_upper(a->n, rp, col, val, order, rp1, col1, val1);
+            if (p->flags & RACE_FLAG_NATURAL_ORDER) race::natural_plan(a->n, *p, s->plan);
+            else race::build_plan(a->n, rp1.data(), col1.data(), *p, s->plan);
+            for (int32_t& v : s->plan.perm) v = order[static_cast<size_t>(v)];
+        } else if (p->flags & RACE_FLAG_NATURAL_ORDER) {
+            race::natural_plan(a->n, *p, s->plan);
+        } else {
+            race::build_plan(a->n, rp.data(), col.data(), *p, s->plan);
+        }
         permute_upper(a->n, rp, col, val, s->plan.perm, s->h_rp, s->h_col, s->h_val64);
     } catch (const std::bad_alloc&) {
         delete s;

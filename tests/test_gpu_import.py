@@ -1,4 +1,4 @@
-"""GPU checks of race_import and RACE_FLAG_PSEUDO_PERIPHERAL through the C
+"""GPU checks of race_import, RACE_FLAG_PSEUDO_PERIPHERAL and RACE_FLAG_RCM through the C
 ABI: an imported device schedule computes bit for bit what the schedule it
 was exported from computes with the deterministic phase executor (a leaf per
 lane group, plain updates of b in a fixed order), and both kinds of schedule
@@ -83,6 +83,20 @@ def test_pseudo_peripheral_schedule_parity(dev, oracle_mod, matgen_mod, name, mk
     s = R.race_build(m, nt, max_depth=md, pseudo_peripheral=True)
     assert s.export() == oracle_mod.Race(m, nt, max_depth=md, pseudo_peripheral=True).export()
     x = matgen_mod.uniform(m["n"], 43, -1.0, 1.0)
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
+    for executor in (R.RACE_EXEC_LEAF_GROUP, R.RACE_EXEC_DF64_RED):
+        assert_parity(run(s, x, dev, executor), bref, sc)
+
+
+@pytest.mark.parametrize("name,mk,nt,md", CASES, ids=[c[0] for c in CASES])
+def test_rcm_schedule_parity(dev, oracle_mod, matgen_mod, name, mk, nt, md):
+    """Schedules built on the reverse Cuthill-McKee relabelled matrix
+    (RACE_FLAG_RCM): equal to the oracle's, parity-green with the phase
+    executor and the default executor."""
+    m = mk(matgen_mod)
+    s = R.race_build(m, nt, max_depth=md, rcm=True)
+    assert s.export() == oracle_mod.Race(m, nt, max_depth=md, rcm=True).export()
+    x = matgen_mod.uniform(m["n"], 44, -1.0, 1.0)
     bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
     for executor in (R.RACE_EXEC_LEAF_GROUP, R.RACE_EXEC_DF64_RED):
         assert_parity(run(s, x, dev, executor), bref, sc)

@@ -32,7 +32,10 @@ def upper_from_edges(n, edges, seed=0):
     rp = [0]
     col, val = [], []
     for r in rows:
-        r = [r[0]] + sorted(set(r[1:]), key=lambda t: t[0])
+        first = {}
+        for c, v in r[1:]:
+            first.setdefault(c, v)  # an edge listed twice is stored once
+        r = [r[0]] + sorted(first.items())
         col += [c for c, _ in r]
         val += [v for _, v in r]
         rp.append(len(col))
