@@ -257,7 +257,8 @@ def run_ours(args):
     nf = 2 * nu - n
     t0 = time.perf_counter()
     stream = torch.cuda.Stream(device=dev)
-    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream)
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
+                     rcm=cfg.get("rcm", False))
     build_s = time.perf_counter() - t0
     lc = cfg["launch"]
     R.race_set_launch(s, 0, **lc)
@@ -337,7 +338,7 @@ def run_ours(args):
     s_nat.free()
     # ---- FP32-stored values (x, b and the row sums stay FP64), same launch -----------------
     s32 = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
-                       val_type=R.RACE_F32, windows=False)
+                       val_type=R.RACE_F32, windows=False, rcm=cfg.get("rcm", False))
     R.race_set_launch(s32, 0, **lc)
     t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
     # the FP32-valued result for x_host, kept for the normwise error against the FP64 oracle
@@ -445,7 +446,7 @@ def run_ours(args):
         "config": {"workload": name, "desc": WORKLOAD_DESC.get(name, name), "n": n, "nnz_upper": nu, "nnz_full": nf,
                    "l2": "inputs larger than L2 (matrix 1.05 GB; x, b rotate over 4+4 buffers of 83 MB)",
                    "schedule": {"n_workers": cfg["n_workers"], "eps": list(cfg["eps"]), "n_phases": info["n_phases"],
-                                "eta": info["eta"], "depth": info["depth"]},
+                                "eta": info["eta"], "depth": info["depth"], "rcm": bool(cfg.get("rcm", False))},
                    "launch": lc, "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
@@ -523,7 +524,7 @@ def run_batch(args):
     tuned = {}
     for i, m in enumerate(mats):
         s = R.race_build(m, configs.BATCH_SCHEDULE["n_workers"], max_depth=configs.BATCH_SCHEDULE["max_depth"],
-                         stream=stream)
+                         stream=stream, rcm=configs.BATCH_SCHEDULE.get("rcm", False))
         n, nu = m["n"], len(m["col"])
         X = configs.matgen.uniform(n * k, 300 + i).reshape(n, k)
         xp = torch.from_numpy(np.ascontiguousarray(X[s.perm()])).to(dev)
@@ -625,7 +626,8 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch64", "k": k, "matrices": len(mats),
-                       "rows": int(sum(m["n"] for m in mats)), "tuned_launches": tuned,
+                       "rows": int(sum(m["n"] for m in mats)), "schedule": dict(configs.BATCH_SCHEDULE),
+                       "tuned_launches": tuned,
                        "l2": "inputs larger than L2 (all matrices and blocks: several GB per replay)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_step": sym_bytes},

@@ -170,7 +170,7 @@ def test_full_size_xxz26(dev, oracle_mod):
     name = "xxz26"
     m = configs.matrix(name)
     cfg = configs.SCHEDULE[name]
-    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"])
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], rcm=cfg.get("rcm", False))
     n = m["n"]
     x = configs.vectors(name, n)
     perm = s.perm()
@@ -204,7 +204,8 @@ def st27_schedule():
         m = configs.matrix(name)
         cfg = configs.SCHEDULE[name]
         _ST27["m"] = m
-        _ST27["s"] = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"])
+        _ST27["s"] = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"],
+                                  rcm=cfg.get("rcm", False))
         lc = cfg["launch"]  # the launch the benchmark times
         R.race_set_launch(_ST27["s"], 0, **lc)
     return _ST27["m"], _ST27["s"]

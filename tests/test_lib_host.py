@@ -203,7 +203,8 @@ def test_full_size_schedules_match_oracle(oracle_mod, name):
     from paper_1907_06487_gb300 import configs
     m = configs.matrix(name)
     cfg = configs.SCHEDULE[name]
-    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], host_only=True)
-    o = oracle_mod.Race(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"])
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], host_only=True,
+                     rcm=cfg.get("rcm", False))
+    o = oracle_mod.Race(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], rcm=cfg.get("rcm", False))
     assert s.export() == o.export()
     s.free()
