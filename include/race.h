@@ -78,6 +78,19 @@ extern "C" {
                                    vertex (Sec. 6.1); this flag gives other
                                    orders the same start.  Recursion roots
                                    are unchanged.                           */
+#define RACE_FLAG_ONE_LEVEL_STAGE0 32u /* stage-0 level groups of one level
+                                   or more instead of two (k = 1 in the
+                                   pairing and balancing of Sec. 4.4.3 at
+                                   stage 0 only).  With upper storage in level
+                                   order a row of level j updates b only in
+                                   levels j and j + 1, so groups of the same
+                                   colour one level apart never share an
+                                   entry of b (they are not distance-2
+                                   independent: an update of every neighbour
+                                   would conflict); up to twice the stage-0
+                                   groups.  Deeper stages keep k = 2: a
+                                   group's halo neighbours are not confined
+                                   to the next sub-level.                   */
 #define RACE_FLAG_RCM 16u /* relabel the matrix by reverse Cuthill-McKee
                                    before the construction, as the paper does
                                    with all of its inputs (Sec. 6.1): each

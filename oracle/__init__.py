@@ -232,14 +232,16 @@ def rcm_order(m):
 class Race:
     """The oracle's RACE schedule for one matrix (Sec. 4-5 of the paper)."""
 
-    def __init__(self, m, n_workers, eps=DEFAULT_EPS, max_depth=-1, balance=0, pseudo_peripheral=False, rcm=False):
+    def __init__(self, m, n_workers, eps=DEFAULT_EPS, max_depth=-1, balance=0, pseudo_peripheral=False, rcm=False,
+                 one_level_stage0=False):
         n, rp, ci, _ = _mat(m)
         e = np.zeros(8)
         e[:len(eps)] = eps
         if len(eps) < 8:
             e[len(eps):] = eps[-1]
         self._h = _get().orc_race(n, _p(rp, _i32p), _p(ci, _i32p), int(n_workers), _p(e, _f64p),
-                                  int(max_depth), int(balance), int(bool(pseudo_peripheral)) | (2 if rcm else 0))
+                                  int(max_depth), int(balance), int(bool(pseudo_peripheral)) | (2 if rcm else 0)
+                                  | (4 if one_level_stage0 else 0))
         if not self._h:
             raise ValueError("oracle race build failed")
         info = np.zeros(6, np.int32)

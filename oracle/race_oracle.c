@@ -66,6 +66,13 @@
  *   R9 phases: P(leaf)=1, P(node) = max P over red children + max P over
  *      blue children; red children start at the node's offset, blue ones
  *      after the red block.  Empty leaves are not listed.
+ *   R10 opt-in: stage-0 level groups need only one level (k = 1 in the
+ *      pairing and balancing of the whole graph).  With upper storage in
+ *      level order a row of level j updates b only in levels j and j + 1
+ *      (lower storage: j - 1 and j), so same-colour groups one level apart
+ *      stay write-disjoint, though not distance-2 independent; deeper
+ *      stages keep k = 2 (halo neighbours are not confined to the next
+ *      sub-level).
  */
 #ifdef _OPENMP
 #include <omp.h>
@@ -294,7 +301,7 @@ typedef struct {
 } onode;
 
 typedef struct {
-    int32_t n, nt, k, balance, max_depth, pp;
+    int32_t n, nt, k, balance, max_depth, pp, one0;
     double eps[8];
     /* graph: full adjacency without self loops */
     int64_t *aptr; int32_t *adj;
@@ -594,12 +601,14 @@ static void split_node(osched *S, int32_t id) {
     int64_t *sz; int32_t *rows;
     int32_t nlev = build_levels(S, nd.lo, nd.hi, whole, &sz, &rows);
     S->nodes[id].nsub = nlev;
-    if (nlev < 2 * S->k) { free(sz); free(rows); return; }
+    /* levels per group: k (= 2); one level at stage 0 when asked (R10) */
+    int32_t k = (whole && S->one0) ? 1 : S->k;
+    if (nlev < 2 * k) { free(sz); free(rows); return; }
     int32_t s = nd.stage + 1;
     double eps = S->eps[s < 8 ? s : 7];
     int32_t *pb = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nlev + 2));
     int32_t *pt = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nlev + 2));
-    int32_t np = make_pairs(sz, nlev, nd.nthreads, eps, S->k, pb, pt);
+    int32_t np = make_pairs(sz, nlev, nd.nthreads, eps, k, pb, pt);
     int32_t len = 2 * np;
     int32_t *tp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)len + 1));
     int32_t *worker = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
@@ -609,7 +618,7 @@ static void split_node(osched *S, int32_t id) {
         worker[2 * p] = worker[2 * p + 1] = pt[p];
     }
     tp[len] = nlev;
-    load_balance(sz, nlev, tp, worker, len, S->k);
+    load_balance(sz, nlev, tp, worker, len, k);
     /* children, in level order */
     int32_t first = S->nnodes;
     int32_t row0 = nd.lo, thr = nd.thread_lo;
@@ -681,7 +690,7 @@ int orc_permute_upper(int32_t n, const int32_t *rp, const int32_t *ci, const dou
 int32_t orc_rcm_order(int32_t n, const int32_t *rp, const int32_t *ci, int32_t *order);
 
 /* options: bit 0 = pseudo-peripheral stage-0 roots, bit 1 = RCM relabelling
- * first (see the readings above).                                         */
+ * first, bit 2 = stage-0 groups of one level (R10; see the readings).     */
 osched *orc_race(int32_t n, const int32_t *rp, const int32_t *ci, int32_t nt, const double *eps8,
                  int32_t max_depth, int32_t balance, int32_t options) {
     if (n <= 0 || nt <= 0) return NULL;
@@ -706,6 +715,7 @@ osched *orc_race(int32_t n, const int32_t *rp, const int32_t *ci, int32_t nt, co
     osched *S = (osched *)calloc(1, sizeof(osched));
     S->n = n; S->nt = nt; S->k = 2; S->balance = balance; S->max_depth = max_depth;
     S->pp = (options & 1) != 0;
+    S->one0 = (options & 4) != 0;
     for (int i = 0; i < 8; ++i) S->eps[i] = eps8[i];
     /* symmetric adjacency (self loops dropped, Sec. 4 graph definitions) */
     S->aptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));

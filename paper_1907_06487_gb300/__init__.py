@@ -38,6 +38,7 @@ RACE_FLAG_NO_WINDOWS = 2
 RACE_FLAG_NATURAL_ORDER = 4
 RACE_FLAG_PSEUDO_PERIPHERAL = 8
 RACE_FLAG_RCM = 16
+RACE_FLAG_ONE_LEVEL_STAGE0 = 32
 
 PAPER_EPS = (0.8, 0.8, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5)
 
@@ -207,7 +208,7 @@ def _check(rc, where):
 
 
 def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0, host_only=False,
-                windows=True, natural_order=False, pseudo_peripheral=False, rcm=False):
+                windows=True, natural_order=False, pseudo_peripheral=False, rcm=False, one_level_stage0=False):
     p = race_params()
     lib().race_default_params(ctypes.byref(p), int(n_workers))
     e = list(eps) + [eps[-1]] * (8 - len(eps))
@@ -218,7 +219,8 @@ def make_params(n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, g
     p.group_lanes = int(group_lanes)
     p.flags = ((RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS)
                | (RACE_FLAG_NATURAL_ORDER if natural_order else 0)
-               | (RACE_FLAG_PSEUDO_PERIPHERAL if pseudo_peripheral else 0) | (RACE_FLAG_RCM if rcm else 0))
+               | (RACE_FLAG_PSEUDO_PERIPHERAL if pseudo_peripheral else 0) | (RACE_FLAG_RCM if rcm else 0)
+               | (RACE_FLAG_ONE_LEVEL_STAGE0 if one_level_stage0 else 0))
     return p
 
 
@@ -295,11 +297,11 @@ def _csr(m, val_type):
 
 def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS, group_lanes=0,
                host_only=False, stream=None, val_type=RACE_F64, windows=True, natural_order=False,
-               pseudo_peripheral=False, rcm=False) -> Schedule:
+               pseudo_peripheral=False, rcm=False, one_level_stage0=False) -> Schedule:
     """race_build on a matrix dict {n, row_ptr, col, val} (host numpy arrays)."""
     a, keep = _csr(m, val_type)
     p = make_params(n_workers, eps, max_depth, balance, group_lanes, host_only, windows, natural_order,
-                    pseudo_peripheral, rcm)
+                    pseudo_peripheral, rcm, one_level_stage0)
     h = ctypes.c_void_p()
     _check(lib().race_build(ctypes.byref(a), ctypes.byref(p), _stream(stream), ctypes.byref(h)), "race_build")
     del keep

@@ -252,8 +252,7 @@ private:
     };
 
     // Sec. 4.4.3 steps 1-3: aggregate levels into pairs of level groups.
-    std::vector<Pair> pair_levels(const LevelSet& ls, int32_t threads, double eps) const {
-        const int32_t k = p_.dist_k;
+    std::vector<Pair> pair_levels(const LevelSet& ls, int32_t threads, double eps, int32_t k) const {
         const int64_t total = std::accumulate(ls.weight.begin(), ls.weight.end(), int64_t{0});
         auto share = [&](int64_t w) {
             return total > 0 ? static_cast<double>(w * static_cast<int64_t>(threads)) / static_cast<double>(total)
@@ -307,8 +306,7 @@ private:
     }
 
     // Alg. "Load Balancing" with worker weights over level groups ptr[].
-    void balance(const LevelSet& ls, std::vector<int32_t>& ptr, const std::vector<int32_t>& worker) const {
-        const int32_t k = p_.dist_k;
+    void balance(const LevelSet& ls, std::vector<int32_t>& ptr, const std::vector<int32_t>& worker, int32_t k) const {
         const int32_t len = static_cast<int32_t>(worker.size());
         std::vector<int64_t> prefix(ls.count + 1, 0);
         for (int32_t l = 0; l < ls.count; ++l) prefix[l + 1] = prefix[l] + ls.weight[l];
@@ -378,10 +376,14 @@ private:
         LevelSet ls = levels(lo, hi, whole);
         plan_.nodes[id].n_sub = ls.count;
         if (whole) plan_.n_levels = ls.count;
-        const int32_t k = p_.dist_k;
+        // levels per group: k = 2 (Sec. 4.2); with RACE_FLAG_ONE_LEVEL_STAGE0
+        // one level per stage-0 group (upper storage in level order: a row of
+        // level j writes b only in levels j and j + 1, so same-colour groups
+        // one level apart stay write-disjoint)
+        const int32_t k = (whole && (p_.flags & RACE_FLAG_ONE_LEVEL_STAGE0)) ? 1 : p_.dist_k;
         if (ls.count < 2 * k) return {};
         const double eps = p_.eps[std::min(stage, 7)];
-        const std::vector<Pair> pairs = pair_levels(ls, threads, eps);
+        const std::vector<Pair> pairs = pair_levels(ls, threads, eps, k);
         std::vector<int32_t> ptr;
         std::vector<int32_t> worker;
         for (const Pair& pr : pairs) {
@@ -391,7 +393,7 @@ private:
             worker.push_back(pr.threads);
         }
         ptr.push_back(ls.count);
-        balance(ls, ptr, worker);
+        balance(ls, ptr, worker, k);
         std::vector<int32_t> kids;
         int32_t row = lo, tid = plan_.nodes[id].thread_lo;
         for (size_t gi = 0; gi + 1 < ptr.size(); ++gi) {

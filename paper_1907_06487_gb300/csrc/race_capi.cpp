@@ -357,7 +357,7 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
     if ((p->flags & RACE_FLAG_PSEUDO_PERIPHERAL) && (p->flags & RACE_FLAG_NATURAL_ORDER))
         return fail(RACE_ERR_INVALID, "RACE_FLAG_PSEUDO_PERIPHERAL has no effect with RACE_FLAG_NATURAL_ORDER");
     if (p->flags & ~(RACE_FLAG_HOST_ONLY | RACE_FLAG_NO_WINDOWS | RACE_FLAG_NATURAL_ORDER | RACE_FLAG_PSEUDO_PERIPHERAL |
-                     RACE_FLAG_RCM))
+                     RACE_FLAG_RCM | RACE_FLAG_ONE_LEVEL_STAGE0))
         return fail(RACE_ERR_INVALID, "unknown flag bits");
 
     race_schedule* s = new (std::nothrow) race_schedule();

@@ -24,10 +24,12 @@
 //   3. one thread per target sums its group and flushes it to b:
 //        RED mode:  reduction at L2 (tiles in any order, one launch);
 //        RACE mode: plain load/add/store.  The tiles of one RACE leaf run in
-//                   order on one block, one launch per phase.  Leaves of a
-//                   phase are distance-2 independent (Eq. "corollary_dk"),
-//                   so their write sets are disjoint: no two blocks touch
-//                   the same entry of b during a phase.
+//                   order on one block, one launch per phase.  The write
+//                   sets of the leaves of a phase are disjoint (distance-2
+//                   independent leaves, Eq. "corollary_dk", or stage-0
+//                   groups of one level, whose rows write b only in their
+//                   own and the next level), and the flush touches W only:
+//                   no two blocks touch the same entry of b during a phase.
 // No atomics in shared memory; in RACE mode none in global memory either.
 #include <cuda_runtime.h>
 

@@ -1,4 +1,5 @@
-"""GPU checks of race_import, RACE_FLAG_PSEUDO_PERIPHERAL and RACE_FLAG_RCM through the C
+"""GPU checks of race_import and of the RACE_FLAG_PSEUDO_PERIPHERAL, RACE_FLAG_RCM and
+RACE_FLAG_ONE_LEVEL_STAGE0 schedules through the C
 ABI: an imported device schedule computes bit for bit what the schedule it
 was exported from computes with the deterministic phase executor (a leaf per
 lane group, plain updates of b in a fixed order), and both kinds of schedule
@@ -99,4 +100,19 @@ def test_rcm_schedule_parity(dev, oracle_mod, matgen_mod, name, mk, nt, md):
     x = matgen_mod.uniform(m["n"], 44, -1.0, 1.0)
     bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
     for executor in (R.RACE_EXEC_LEAF_GROUP, R.RACE_EXEC_DF64_RED):
+        assert_parity(run(s, x, dev, executor), bref, sc)
+
+
+@pytest.mark.parametrize("name,mk,nt,md", CASES, ids=[c[0] for c in CASES])
+def test_one_level_stage0_parity(dev, oracle_mod, matgen_mod, name, mk, nt, md):
+    """Stage-0 groups of one level (RACE_FLAG_ONE_LEVEL_STAGE0): the phase
+    executors, which update b with plain stores inside a leaf (0), with
+    reductions inside a leaf (1) and through shared-memory windows flushed
+    with plain stores (7), stay parity-green on them."""
+    m = mk(matgen_mod)
+    s = R.race_build(m, nt, max_depth=md, one_level_stage0=True)
+    assert s.export() == oracle_mod.Race(m, nt, max_depth=md, one_level_stage0=True).export()
+    x = matgen_mod.uniform(m["n"], 45, -1.0, 1.0)
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
+    for executor in (R.RACE_EXEC_LEAF_GROUP, R.RACE_EXEC_LEAF_CTA, R.RACE_EXEC_WINDOW_RACE, R.RACE_EXEC_DF64_RED):
         assert_parity(run(s, x, dev, executor), bref, sc)
