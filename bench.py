@@ -321,7 +321,8 @@ def run_ours(args):
     # ---- the conflict-free RACE executors (a few steps: they are slow) on the schedule that
     # suits them (full recursion), one row per thread in the leaf executor
     cf = cfg["conflict_free"]
-    s_cf = R.race_build(m, cf["n_workers"], eps=cfg["eps"], max_depth=cf["max_depth"], stream=stream)
+    s_cf = R.race_build(m, cf["n_workers"], eps=cfg["eps"], max_depth=cf["max_depth"], stream=stream,
+                        one_level_stage0=cf.get("one_level_stage0", False))
     info_cf = s_cf.info()
     R.race_set_launch(s_cf, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
     t_leaf_cta = timed(lambda i: R.symm_spmv(s_cf, xs[i % ring], bs[i % ring], stream), 3, 1)
@@ -474,6 +475,7 @@ def run_ours(args):
         "race_conflict_free": {"leaf_cta_ms_per_step": t_leaf_cta / 3 * 1e3,
                                "window_race_ms_per_step": t_win_race / 3 * 1e3,
                                "schedule": {"n_workers": cf["n_workers"], "max_depth": cf["max_depth"],
+                                            "one_level_stage0": bool(cf.get("one_level_stage0", False)),
                                             "n_phases": info_cf["n_phases"], "n_leaves": info_cf["n_leaves"],
                                             "eta": info_cf["eta"]},
                                "what": "RACE_EXEC_LEAF_CTA and RACE_EXEC_WINDOW_RACE (phase by phase, no two concurrent "
