@@ -39,6 +39,7 @@
 #include <numeric>
 
 #include "race_internal.h"
+#include "race_plan_ops.h"
 
 namespace race {
 namespace {

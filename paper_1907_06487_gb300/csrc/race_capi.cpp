@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "race_internal.h"
+#include "race_plan_ops.h"
 
 namespace {
 thread_local std::string g_detail;

@@ -42,24 +42,12 @@ struct Plan {
 // rows are canonical (diagonal first, strictly increasing columns).
 void build_plan(int32_t n, const int32_t* row_ptr, const int32_t* col, const race_params& p, Plan& out);
 
-// Reverse Cuthill-McKee order (order[new] = old) of the symmetric graph of a
-// canonical upper CRS: components in the order of their lowest vertex, each
-// from a pseudo-peripheral vertex of it, breadth first with the neighbours
-// newly reached from a vertex taken by increasing degree (lowest index on
-// ties); the whole sequence reversed.
-std::vector<int32_t> rcm_order(int32_t n, const int32_t* row_ptr, const int32_t* col);
-
 // The plan of RACE_FLAG_NATURAL_ORDER: identity permutation, one phase
 // holding one leaf with every row.
 void natural_plan(int32_t n, const race_params& p, Plan& out);
 
 // Canonical export image (layout documented in race.h).
 std::vector<uint8_t> export_plan(const Plan& plan);
-
-// Inverse of export_plan for a matrix of n rows: every field is checked
-// (sizes, permutation, phase offsets, leaves covering each row exactly
-// once, the tree's shape); false with the reason in `why` on any mismatch.
-bool import_plan(const void* buf, size_t size, int32_t n, Plan& out, std::string& why);
 
 }  // namespace race
 
