@@ -164,7 +164,9 @@ void race_default_params(race_params *p, int32_t n_workers);
  * symmetrically and uploaded to the device on `stream` (unless
  * RACE_FLAG_HOST_ONLY); the call returns after the upload has completed.
  * On success *out owns host and device copies until race_free.
- * Errors: RACE_ERR_INVALID, _OVERFLOW, _NOMEM, _CUDA.                      */
+ * Errors: RACE_ERR_INVALID (malformed matrix or parameters, unknown flag
+ * bits, RACE_FLAG_PSEUDO_PERIPHERAL together with RACE_FLAG_NATURAL_ORDER),
+ * _UNSUPPORTED (dist_k other than 2), _OVERFLOW, _NOMEM, _CUDA.            */
 int race_build(const race_csr_upper *a, const race_params *p, void *stream, race_schedule **out);
 
 /* race_upload — turns a schedule built with RACE_FLAG_HOST_ONLY into a
