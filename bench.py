@@ -211,6 +211,11 @@ def oracle_normwise_error(m, x, b_perm, perm):
     return float(np.linalg.norm(b - bref) / np.linalg.norm(s))
 
 
+# the metric of both arms (the reference arm times the oracle's RACE
+# SymmSpMV on the host cores under the same name, unit and direction)
+METRIC_SYMM = "SymmSpMV GFLOP/s (2*nnz_full flops per step) on 1 GB300 vs full-CRS SpMV"
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -219,7 +224,7 @@ def run_reference(args):
     m = configs.matrix(args.workload)
     cpu = oracle_cpu(m, args.workload, max(3.0, args.ref_seconds))
     line = {
-        "impl": "reference", "metric": "SymmSpMV GFLOP/s (2*nnz_full flops per step)", "value": cpu["value"],
+        "impl": "reference", "metric": METRIC_SYMM, "value": cpu["value"],
         "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": cpu["ms_per_sweep"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -440,7 +445,7 @@ def run_ours(args):
         fp32_err = oracle_normwise_error(m, x_host, b32_perm, perm)
     traffic = ncu_traffic(name, "symm")
     line = {
-        "metric": "SymmSpMV GFLOP/s (2*nnz_full flops per step) on 1 GB300 vs full-CRS SpMV",
+        "metric": METRIC_SYMM,
         "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
