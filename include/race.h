@@ -344,8 +344,12 @@ int race_export(const race_schedule *s, void *buf, size_t *size);
  * RACE_FLAG_NO_WINDOWS, as for race_build.  The launch shape starts at the
  * defaults of race_build and group_lanes is automatic.  race_export of the
  * result reproduces the image byte for byte.
- * Errors: RACE_ERR_INVALID (malformed image, or an image of another
- * matrix; reason in race_last_error_detail), _OVERFLOW, _NOMEM, _CUDA.      */
+ * An image built from another matrix of the same size is refused when its
+ * phases conflict on this one; if they happen not to, it is accepted (the
+ * executors need only that) and keeps the other matrix's tree statistics
+ * (eta, N_eff, levels).
+ * Errors: RACE_ERR_INVALID (malformed image, or phases that conflict on this
+ * matrix; reason in race_last_error_detail), _OVERFLOW, _NOMEM, _CUDA.     */
 int race_import(const race_csr_upper *a, const void *image, size_t size, uint32_t flags, void *stream,
                 race_schedule **out);
 
