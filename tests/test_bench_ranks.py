@@ -1,7 +1,7 @@
-"""The multi-rank host logic of bench.py on CPU: two gloo ranks (the N > 1
+"""The host logic of bench.py on CPU: two gloo ranks (the N > 1
 path runs independent replicas, so its only exchange is the max over ranks
 of the timings), the whole-job throughput, and the reference arm's rule that
-ranks other than 0 exit without work."""
+ranks other than 0 exit without work; and the reference arm's JSON line."""
 import os
 import socket
 import sys
@@ -61,3 +61,31 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     args = bench.build_parser().parse_args(["--impl", "reference", "--gpus", "2"])
     assert bench.run_reference(args) == 0
+
+
+def test_reference_arm_line(tmp_path):
+    """bench.py --impl reference on one process: one JSON line with the
+    contract's keys, the oracle timed on the host cores under our arm's metric
+    name, no host-device bytes (CPU only)."""
+    import json
+    import subprocess
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "anderson32", "--steps", "3", "--warmup", "3", "--ref-seconds", "1"],
+                         capture_output=True, text=True, env=env, cwd=str(tmp_path), timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC_SYMM
+    for key in ("value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["value"] > 0 and d["unit"] == "GFLOP/s" and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "anderson32"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
