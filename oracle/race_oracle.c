@@ -22,6 +22,7 @@
  *                      the paper's own execution model (OpenMP)
  *   orc_spmv_full_par  Alg. "SpMV using the CRS format" with its rows split
  *                      over CPU threads (OpenMP), no s
+ *   orc_symm_gs        symmetric Gauss-Seidel sweeps under a schedule (R11)
  *
  * Schedule part (integer + FP64 control arithmetic), Section 4:
  *   level construction (Alg. "Construction of levels", Eq. "level"),
@@ -73,6 +74,10 @@
  *      stay write-disjoint, though not distance-2 independent; deeper
  *      stages keep k = 2 (halo neighbours are not confined to the next
  *      sub-level).
+ *   R11 symmetric Gauss-Seidel on a schedule: the serial sweep in the
+ *      schedule's execution order (forward: phases in order, rows of a leaf
+ *      ascending; backward: phases reversed, rows descending), on the full
+ *      matrix in the schedule's order.
  */
 #ifdef _OPENMP
 #include <omp.h>
@@ -908,6 +913,38 @@ int orc_check_phases(int32_t n, const int32_t *prp, const int32_t *pci, int32_t 
     for (int32_t i = 0; i < n && !rc; ++i) if (cover[i] != 1) rc = 1;
     free(cover); free(owner); free(ophase);
     return rc;
+}
+
+/* Symmetric Gauss-Seidel under a flattened schedule (R11: the paper names
+ * Gauss-Seidel among the kernels with distance-k dependencies that RACE
+ * schedules serve).  One sweep = a forward pass, phases in order, the rows of every leaf in
+ * ascending order, then a backward pass, phases in reverse order, the rows
+ * of every leaf in descending order; each row update
+ *     x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii
+ * reads the current x.  Leaves of a phase share no edge (the schedules are
+ * distance-2 colourings, stronger than the distance 1 Gauss-Seidel needs),
+ * so the leaf order inside a phase does not change the result.  Full CRS
+ * (frp int64) of the matrix in the schedule's order; x updated in place.  */
+void orc_symm_gs(int32_t n, const int64_t *frp, const int32_t *fci, const double *fva, int32_t nphases,
+                 const int32_t *stage_ptr, const int32_t *lo, const int32_t *hi, const double *b, double *x,
+                 int32_t sweeps) {
+    (void)n;
+    for (int32_t sw = 0; sw < sweeps; ++sw) {
+        for (int32_t dir = 0; dir < 2; ++dir)
+            for (int32_t pi = 0; pi < nphases; ++pi) {
+                int32_t ph = dir == 0 ? pi : nphases - 1 - pi;
+                for (int32_t q = stage_ptr[ph]; q < stage_ptr[ph + 1]; ++q)
+                    for (int32_t k = 0; k < hi[q] - lo[q]; ++k) {
+                        int32_t r = dir == 0 ? lo[q] + k : hi[q] - 1 - k;
+                        double s = b[r], d = 0.0;
+                        for (int64_t t = frp[r]; t < frp[r + 1]; ++t) {
+                            if (fci[t] == r) d += fva[t];
+                            else s -= fva[t] * x[fci[t]];
+                        }
+                        x[r] = s / d;
+                    }
+            }
+    }
 }
 
 /* The pseudo-peripheral vertex reached from `start` on the symmetric graph
