@@ -300,6 +300,21 @@ int symm_spmm(const race_schedule *s, int32_t k, const double *X_d, double *B_d,
  * by race_prepare_full) and kept with the schedule.  k = 1.               */
 int spmv_full(const race_schedule *s, const double *x_d, double *b_d, void *stream);
 
+/* symm_gs — `sweeps` symmetric Gauss-Seidel sweeps for A x = b under the
+ * schedule (the paper names Gauss-Seidel among the kernels with distance-k
+ * dependencies that RACE serves): a forward pass over the phases in order,
+ * the rows of each leaf ascending, then a backward pass over the phases in
+ * reverse, rows descending; each row x_i <- (b_i - sum_{j != i} a_ij x_j) /
+ * a_ii from the current x.  Leaves of a phase share no edge, so the result
+ * is the serial sweep in that execution order.  b_d (input) and x_d (start
+ * value in, result out) are caller-owned device arrays of n doubles in
+ * permuted order and must not alias; the full CRS is built on first use as
+ * for spmv_full.  One launch per phase and pass on `stream`.  A zero
+ * diagonal gives inf or nan entries.
+ * Errors: RACE_ERR_INVALID (NULL, aliasing, sweeps < 0), _UNSUPPORTED
+ * (host-only schedule), _OVERFLOW, _NOMEM, _CUDA.                          */
+int symm_gs(const race_schedule *s, const double *b_d, double *x_d, int32_t sweeps, void *stream);
+
 /* Build and upload the full CRS used by spmv_full now (optional).          */
 int race_prepare_full(race_schedule *s, void *stream);
 

@@ -1,0 +1,132 @@
+// Symmetric Gauss-Seidel sweeps under a RACE schedule: the paper names
+// Gauss-Seidel among the kernels with distance-k dependencies that the same
+// schedules serve.
+//
+// One sweep is a forward pass over the phases in order and a backward pass
+// over them in reverse order.  Inside a phase every leaf runs on one group of
+// G lanes, its rows one after the other (ascending forward, descending
+// backward), each updated in place from the current x:
+//     x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii
+// on the full CRS of the permuted matrix (built once, as for spmv_full).
+// Leaves of a phase share no edge (the schedules are distance-2 colourings,
+// stronger than the distance 1 this kernel needs), so no lane reads an entry
+// of x that another leaf of the phase writes; inside a leaf the group
+// synchronises after every row, so the next row reads the new value.  One
+// launch per phase and pass.  A zero diagonal gives inf or nan, as the serial
+// method would; nothing traps.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "race_internal.h"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+// One phase of one pass: leaf q of the phase on lanes [q*G, q*G + G).
+template <typename VT, int G, bool BACKWARD>
+__global__ void __launch_bounds__(kBlock) k_gs_phase(const int32_t* __restrict__ frp, const int32_t* __restrict__ fcol,
+                                                    const VT* __restrict__ fval, const double* __restrict__ b,
+                                                    double* x, const int32_t* __restrict__ leaf_lo,
+                                                    const int32_t* __restrict__ leaf_hi, int32_t nleaves) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const int64_t leaf = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
+    if (leaf >= nleaves) return;  // all G lanes of a group share the leaf index
+    const int32_t lo = __ldg(leaf_lo + leaf), hi = __ldg(leaf_hi + leaf);
+    for (int32_t k = 0; k < hi - lo; ++k) {
+        const int32_t r = BACKWARD ? hi - 1 - k : lo + k;
+        double s = 0.0, d = 0.0;
+        const int32_t end = __ldg(frp + r + 1);
+        for (int32_t t = __ldg(frp + r) + lane; t < end; t += G) {
+            const int32_t c = __ldg(fcol + t);
+            const double a = static_cast<double>(__ldg(fval + t));
+            if (c == r) d += a;
+            else s += a * x[c];  // plain load: x changes during the launch
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(mask, s, o, G);
+            d += __shfl_xor_sync(mask, d, o, G);
+        }
+        if (lane == 0) x[r] = (__ldg(b + r) - s) / d;
+        __syncwarp(mask);  // the group's next row reads x[r]
+    }
+}
+
+template <typename VT, int G>
+void sweep(const race_schedule* s, const double* b, double* x, int32_t sweeps, cudaStream_t st) {
+    const auto& sp = s->plan.stage_ptr;
+    const int32_t nph = static_cast<int32_t>(sp.size()) - 1;
+    const VT* fval = static_cast<const VT*>(s->d_fval);
+    for (int32_t w = 0; w < sweeps; ++w)
+        for (int pass = 0; pass < 2; ++pass)
+            for (int32_t i = 0; i < nph; ++i) {
+                const int32_t p = pass == 0 ? i : nph - 1 - i;
+                const int32_t nl = sp[p + 1] - sp[p];
+                if (nl == 0) continue;
+                const int grid = static_cast<int>((static_cast<int64_t>(nl) * G + kBlock - 1) / kBlock);
+                if (pass == 0)
+                    k_gs_phase<VT, G, false><<<grid, kBlock, 0, st>>>(s->d_frp, s->d_fcol, fval, b, x,
+                                                                     s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
+                else
+                    k_gs_phase<VT, G, true><<<grid, kBlock, 0, st>>>(s->d_frp, s->d_fcol, fval, b, x,
+                                                                    s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
+            }
+}
+
+template <typename VT>
+void sweep_vt(const race_schedule* s, const double* b, double* x, int32_t sweeps, cudaStream_t st) {
+    switch (s->group_lanes) {
+        case 4: sweep<VT, 4>(s, b, x, sweeps, st); break;
+        case 16: sweep<VT, 16>(s, b, x, sweeps, st); break;
+        case 32: sweep<VT, 32>(s, b, x, sweeps, st); break;
+        default: sweep<VT, 8>(s, b, x, sweeps, st); break;
+    }
+}
+
+}  // namespace
+
+extern "C" int symm_gs(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, void* stream) {
+    if (!s || !b_d || !x_d) {
+        race_set_detail("NULL argument");
+        return RACE_ERR_INVALID;
+    }
+    if (s->host_only) {
+        race_set_detail("schedule was built with RACE_FLAG_HOST_ONLY");
+        return RACE_ERR_UNSUPPORTED;
+    }
+    if (static_cast<const void*>(b_d) == static_cast<const void*>(x_d)) {
+        race_set_detail("b and x alias");
+        return RACE_ERR_INVALID;
+    }
+    if (sweeps < 0) {
+        race_set_detail("sweeps < 0");
+        return RACE_ERR_INVALID;
+    }
+    if (!s->d_frp) {
+        const int rc = race_prepare_full(const_cast<race_schedule*>(s), stream);
+        if (rc) return rc;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->val_type == RACE_F64) sweep_vt<double>(s, b_d, x_d, sweeps, st);
+    else sweep_vt<float>(s, b_d, x_d, sweeps, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("symm_gs: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    return RACE_OK;
+}
