@@ -315,6 +315,16 @@ int spmv_full(const race_schedule *s, const double *x_d, double *b_d, void *stre
  * (host-only schedule), _OVERFLOW, _NOMEM, _CUDA.                          */
 int symm_gs(const race_schedule *s, const double *b_d, double *x_d, int32_t sweeps, void *stream);
 
+/* symm_kacz — `sweeps` symmetric Kaczmarz sweeps for A x = b under the
+ * schedule (the paper names the Kaczmarz solver among the kernels RACE
+ * serves): the passes of symm_gs, each row projecting x onto its hyperplane,
+ * f = (b_i - sum_j a_ij x_j) / sum_j a_ij^2, x_j += f a_ij for every stored
+ * column j of the row.  A row update writes x at all its columns, so
+ * concurrent leaves must share no column: the schedule's distance-2
+ * independence.  Arguments, layout and errors as for symm_gs; a zero row
+ * gives inf or nan entries.                                                */
+int symm_kacz(const race_schedule *s, const double *b_d, double *x_d, int32_t sweeps, void *stream);
+
 /* Build and upload the full CRS used by spmv_full now (optional).          */
 int race_prepare_full(race_schedule *s, void *stream);
 

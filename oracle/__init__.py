@@ -91,6 +91,9 @@ def _get():
     L.orc_pseudo_peripheral.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32]
     L.orc_rcm_order.restype = ctypes.c_int32
     L.orc_symm_gs.restype = None
+    L.orc_symm_kacz.restype = None
+    L.orc_symm_kacz.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p, _i32p, _f64p,
+                                _f64p, ctypes.c_int32]
     L.orc_symm_gs.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p, _i32p, _f64p,
                               _f64p, ctypes.c_int32]
     L.orc_rcm_order.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
@@ -238,6 +241,23 @@ def symm_gs(full, stage_ptr, lo, hi, b, x0, sweeps=1):
     x = np.array(x0, dtype=np.float64, copy=True)
     _get().orc_symm_gs(n, _p(frp, _i64p), _p(fci, _i32p), _p(fva, _f64p), len(sp) - 1, _p(sp, _i32p),
                        _p(lo, _i32p), _p(hi, _i32p), _p(b, _f64p), _p(x, _f64p), int(sweeps))
+    return x
+
+
+def symm_kacz(full, stage_ptr, lo, hi, b, x0, sweeps=1):
+    """Symmetric Kaczmarz sweeps under a flattened schedule on a full CRS
+    dict (same passes as symm_gs; each row projects x onto its hyperplane)."""
+    n = int(full["n"])
+    frp = np.ascontiguousarray(full["row_ptr"], dtype=np.int64)
+    fci = np.ascontiguousarray(full["col"], dtype=np.int32)
+    fva = np.ascontiguousarray(full["val"], dtype=np.float64)
+    sp = np.ascontiguousarray(stage_ptr, dtype=np.int32)
+    lo = np.ascontiguousarray(lo, dtype=np.int32)
+    hi = np.ascontiguousarray(hi, dtype=np.int32)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64, copy=True)
+    _get().orc_symm_kacz(n, _p(frp, _i64p), _p(fci, _i32p), _p(fva, _f64p), len(sp) - 1, _p(sp, _i32p),
+                         _p(lo, _i32p), _p(hi, _i32p), _p(b, _f64p), _p(x, _f64p), int(sweeps))
     return x
 
 

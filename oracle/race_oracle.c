@@ -23,6 +23,7 @@
  *   orc_spmv_full_par  Alg. "SpMV using the CRS format" with its rows split
  *                      over CPU threads (OpenMP), no s
  *   orc_symm_gs        symmetric Gauss-Seidel sweeps under a schedule (R11)
+ *   orc_symm_kacz      symmetric Kaczmarz sweeps under a schedule (R12)
  *
  * Schedule part (integer + FP64 control arithmetic), Section 4:
  *   level construction (Alg. "Construction of levels", Eq. "level"),
@@ -78,6 +79,8 @@
  *      schedule's execution order (forward: phases in order, rows of a leaf
  *      ascending; backward: phases reversed, rows descending), on the full
  *      matrix in the schedule's order.
+ *   R12 symmetric Kaczmarz on a schedule: the same passes, each row
+ *      projecting x onto its hyperplane (writes every column of the row).
  */
 #ifdef _OPENMP
 #include <omp.h>
@@ -942,6 +945,35 @@ void orc_symm_gs(int32_t n, const int64_t *frp, const int32_t *fci, const double
                             else s -= fva[t] * x[fci[t]];
                         }
                         x[r] = s / d;
+                    }
+            }
+    }
+}
+
+/* Symmetric Kaczmarz under a flattened schedule (R12: the paper names the
+ * Kaczmarz solver among the kernels RACE serves).  Same passes as
+ * orc_symm_gs; a row update projects x onto the row's hyperplane,
+ *     f = (b_i - sum_j a_ij x_j) / sum_j a_ij^2,   x_j <- x_j + f a_ij  (all j),
+ * so it writes x at every column of the row: rows of concurrent leaves must
+ * share no column, which distance-2 independence gives.                   */
+void orc_symm_kacz(int32_t n, const int64_t *frp, const int32_t *fci, const double *fva, int32_t nphases,
+                   const int32_t *stage_ptr, const int32_t *lo, const int32_t *hi, const double *b, double *x,
+                   int32_t sweeps) {
+    (void)n;
+    for (int32_t sw = 0; sw < sweeps; ++sw) {
+        for (int32_t dir = 0; dir < 2; ++dir)
+            for (int32_t pi = 0; pi < nphases; ++pi) {
+                int32_t ph = dir == 0 ? pi : nphases - 1 - pi;
+                for (int32_t q = stage_ptr[ph]; q < stage_ptr[ph + 1]; ++q)
+                    for (int32_t k = 0; k < hi[q] - lo[q]; ++k) {
+                        int32_t r = dir == 0 ? lo[q] + k : hi[q] - 1 - k;
+                        double dot = 0.0, nrm = 0.0;
+                        for (int64_t t = frp[r]; t < frp[r + 1]; ++t) {
+                            dot += fva[t] * x[fci[t]];
+                            nrm += fva[t] * fva[t];
+                        }
+                        double f = (b[r] - dot) / nrm;
+                        for (int64_t t = frp[r]; t < frp[r + 1]; ++t) x[fci[t]] += f * fva[t];
                     }
             }
     }

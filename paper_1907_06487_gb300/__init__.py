@@ -49,7 +49,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status", "race_probe_scatter",
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
-            "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs")
+            "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -124,6 +124,7 @@ def lib():
     L.symm_spmv_exec.argtypes = [vp, i32, vp, vp, vp]
     L.race_prepare_full.argtypes = [vp, vp]
     L.symm_gs.argtypes = [vp, vp, vp, i32, vp]
+    L.symm_kacz.argtypes = [vp, vp, vp, i32, vp]
     L.race_permute.argtypes = [vp, vp, vp, i32, vp]
     L.race_unpermute.argtypes = [vp, vp, vp, i32, vp]
     L.race_get_perm.argtypes = [vp, vp]
@@ -177,7 +178,7 @@ def lib():
     L.race_last_error_detail.restype = ctypes.c_char_p
     for name in ("race_build", "symm_spmv", "symm_spmv_exec", "symm_spmm", "spmv_full", "race_prepare_full", "race_permute",
                  "race_unpermute", "race_get_perm", "race_get_matrix", "race_get_phases", "race_get_info",
-                 "race_export", "race_import", "symm_gs"):
+                 "race_export", "race_import", "symm_gs", "symm_kacz"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -328,6 +329,11 @@ def symm_spmv(s: Schedule, x, b, stream=None):
 def symm_gs(s: Schedule, b, x, sweeps=1, stream=None):
     """symm_gs: `sweeps` symmetric Gauss-Seidel sweeps on x (in place, permuted order)."""
     _check(lib().symm_gs(s.handle, _ptr(b), _ptr(x), int(sweeps), _stream(stream)), "symm_gs")
+
+
+def symm_kacz(s: Schedule, b, x, sweeps=1, stream=None):
+    """symm_kacz: `sweeps` symmetric Kaczmarz sweeps on x (in place, permuted order)."""
+    _check(lib().symm_kacz(s.handle, _ptr(b), _ptr(x), int(sweeps), _stream(stream)), "symm_kacz")
 
 
 def race_set_launch(s: Schedule, which, executor=0, group_lanes=8, rows_per_group=4, blocks_per_sm=0,

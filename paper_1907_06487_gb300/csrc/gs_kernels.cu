@@ -1,6 +1,6 @@
-// Symmetric Gauss-Seidel sweeps under a RACE schedule: the paper names
-// Gauss-Seidel among the kernels with distance-k dependencies that the same
-// schedules serve.
+// Symmetric Gauss-Seidel and symmetric Kaczmarz sweeps under a RACE
+// schedule: the paper names both solvers among the kernels with distance-k
+// dependencies that the same schedules serve.
 //
 // One sweep is a forward pass over the phases in order and a backward pass
 // over them in reverse order.  Inside a phase every leaf runs on one group of
@@ -14,6 +14,13 @@
 // synchronises after every row, so the next row reads the new value.  One
 // launch per phase and pass.  A zero diagonal gives inf or nan, as the serial
 // method would; nothing traps.
+//
+// Kaczmarz projects x onto row i's hyperplane instead,
+//     f = (b_i - sum_j a_ij x_j) / sum_j a_ij^2,   x_j <- x_j + f a_ij  (all j),
+// writing x at every column of the row: rows of concurrent leaves share no
+// column (distance-2 independence), and the lanes of a group update distinct
+// columns of their row.  The butterfly reductions leave every lane of the
+// group with the same f.  A zero row gives inf or nan.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -36,7 +43,7 @@ __device__ __forceinline__ unsigned group_mask() {
 }
 
 // One phase of one pass: leaf q of the phase on lanes [q*G, q*G + G).
-template <typename VT, int G, bool BACKWARD>
+template <typename VT, int G, bool BACKWARD, bool KACZ>
 __global__ void __launch_bounds__(kBlock) k_gs_phase(const int32_t* __restrict__ frp, const int32_t* __restrict__ fcol,
                                                     const VT* __restrict__ fval, const double* __restrict__ b,
                                                     double* x, const int32_t* __restrict__ leaf_lo,
@@ -48,25 +55,35 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(const int32_t* __restrict__
     const int32_t lo = __ldg(leaf_lo + leaf), hi = __ldg(leaf_hi + leaf);
     for (int32_t k = 0; k < hi - lo; ++k) {
         const int32_t r = BACKWARD ? hi - 1 - k : lo + k;
-        double s = 0.0, d = 0.0;
-        const int32_t end = __ldg(frp + r + 1);
-        for (int32_t t = __ldg(frp + r) + lane; t < end; t += G) {
+        double s = 0.0, d = 0.0;  // Gauss-Seidel: off-diagonal sum, diagonal; Kaczmarz: a.x, |a|^2
+        const int32_t beg = __ldg(frp + r), end = __ldg(frp + r + 1);
+        for (int32_t t = beg + lane; t < end; t += G) {
             const int32_t c = __ldg(fcol + t);
             const double a = static_cast<double>(__ldg(fval + t));
-            if (c == r) d += a;
-            else s += a * x[c];  // plain load: x changes during the launch
+            if constexpr (KACZ) {
+                s += a * x[c];  // plain load: x changes during the launch
+                d += a * a;
+            } else {
+                if (c == r) d += a;
+                else s += a * x[c];
+            }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             s += __shfl_xor_sync(mask, s, o, G);
             d += __shfl_xor_sync(mask, d, o, G);
         }
-        if (lane == 0) x[r] = (__ldg(b + r) - s) / d;
-        __syncwarp(mask);  // the group's next row reads x[r]
+        if constexpr (KACZ) {
+            const double f = (__ldg(b + r) - s) / d;
+            for (int32_t t = beg + lane; t < end; t += G) x[__ldg(fcol + t)] += f * static_cast<double>(__ldg(fval + t));
+        } else {
+            if (lane == 0) x[r] = (__ldg(b + r) - s) / d;
+        }
+        __syncwarp(mask);  // the group's next row reads the updated x
     }
 }
 
-template <typename VT, int G>
+template <typename VT, int G, bool KACZ>
 void sweep(const race_schedule* s, const double* b, double* x, int32_t sweeps, cudaStream_t st) {
     const auto& sp = s->plan.stage_ptr;
     const int32_t nph = static_cast<int32_t>(sp.size()) - 1;
@@ -79,27 +96,26 @@ void sweep(const race_schedule* s, const double* b, double* x, int32_t sweeps, c
                 if (nl == 0) continue;
                 const int grid = static_cast<int>((static_cast<int64_t>(nl) * G + kBlock - 1) / kBlock);
                 if (pass == 0)
-                    k_gs_phase<VT, G, false><<<grid, kBlock, 0, st>>>(s->d_frp, s->d_fcol, fval, b, x,
+                    k_gs_phase<VT, G, false, KACZ><<<grid, kBlock, 0, st>>>(s->d_frp, s->d_fcol, fval, b, x,
                                                                      s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
                 else
-                    k_gs_phase<VT, G, true><<<grid, kBlock, 0, st>>>(s->d_frp, s->d_fcol, fval, b, x,
+                    k_gs_phase<VT, G, true, KACZ><<<grid, kBlock, 0, st>>>(s->d_frp, s->d_fcol, fval, b, x,
                                                                     s->d_leaf_lo + sp[p], s->d_leaf_hi + sp[p], nl);
             }
 }
 
-template <typename VT>
+template <typename VT, bool KACZ>
 void sweep_vt(const race_schedule* s, const double* b, double* x, int32_t sweeps, cudaStream_t st) {
     switch (s->group_lanes) {
-        case 4: sweep<VT, 4>(s, b, x, sweeps, st); break;
-        case 16: sweep<VT, 16>(s, b, x, sweeps, st); break;
-        case 32: sweep<VT, 32>(s, b, x, sweeps, st); break;
-        default: sweep<VT, 8>(s, b, x, sweeps, st); break;
+        case 4: sweep<VT, 4, KACZ>(s, b, x, sweeps, st); break;
+        case 16: sweep<VT, 16, KACZ>(s, b, x, sweeps, st); break;
+        case 32: sweep<VT, 32, KACZ>(s, b, x, sweeps, st); break;
+        default: sweep<VT, 8, KACZ>(s, b, x, sweeps, st); break;
     }
 }
 
-}  // namespace
-
-extern "C" int symm_gs(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, void* stream) {
+template <bool KACZ>
+int run(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, void* stream, const char* name) {
     if (!s || !b_d || !x_d) {
         race_set_detail("NULL argument");
         return RACE_ERR_INVALID;
@@ -121,12 +137,22 @@ extern "C" int symm_gs(const race_schedule* s, const double* b_d, double* x_d, i
         if (rc) return rc;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s->val_type == RACE_F64) sweep_vt<double>(s, b_d, x_d, sweeps, st);
-    else sweep_vt<float>(s, b_d, x_d, sweeps, st);
+    if (s->val_type == RACE_F64) sweep_vt<double, KACZ>(s, b_d, x_d, sweeps, st);
+    else sweep_vt<float, KACZ>(s, b_d, x_d, sweeps, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
-        race_set_detail(std::string("symm_gs: ") + cudaGetErrorString(e));
+        race_set_detail(std::string(name) + ": " + cudaGetErrorString(e));
         return RACE_ERR_CUDA;
     }
     return RACE_OK;
+}
+
+}  // namespace
+
+extern "C" int symm_gs(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, void* stream) {
+    return run<false>(s, b_d, x_d, sweeps, stream, "symm_gs");
+}
+
+extern "C" int symm_kacz(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, void* stream) {
+    return run<true>(s, b_d, x_d, sweeps, stream, "symm_kacz");
 }

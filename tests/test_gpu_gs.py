@@ -1,5 +1,6 @@
-"""GPU parity of symm_gs (symmetric Gauss-Seidel under a RACE schedule,
-through the C ABI) against the oracle's orc_symm_gs on the same schedule.
+"""GPU parity of symm_gs and symm_kacz (symmetric Gauss-Seidel and symmetric
+Kaczmarz under a RACE schedule, through the C ABI) against the oracle's
+orc_symm_gs and orc_symm_kacz on the same schedule.
 
 The matrices are diagonally dominant (diagonal = row abs sum + 1), so a sweep
 is contractive: a rounding difference in one row (the kernel sums a row in
@@ -83,3 +84,30 @@ def test_symm_gs_edges(dev, matgen_mod):
     with pytest.raises(R.RaceError) as e:
         R.symm_gs(h, b, x, 1)
     assert e.value.code == R.RACE_ERR_UNSUPPORTED
+
+
+KACZ_CASES = CASES + [("anderson12", lambda g: g.anderson(12, seed=1), 48, {})]
+
+
+@pytest.mark.parametrize("name,mk,nt,kw", KACZ_CASES, ids=[c[0] for c in KACZ_CASES])
+def test_symm_kacz_parity(dev, oracle_mod, matgen_mod, name, mk, nt, kw):
+    """symm_kacz against the oracle.  Row projections are nonexpansive, so a
+    rounding difference (another summation order of a.x and |a|^2) is not
+    amplified by later rows: bound 1e-12 of the largest entry of x."""
+    m = mk(matgen_mod)
+    s = R.race_build(m, nt, **kw)
+    full = oracle_mod.expand_full(s.matrix())
+    sp, lo, hi = s.phases()
+    n = m["n"]
+    rng = np.random.default_rng(13)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    want = oracle_mod.symm_kacz(full, sp, lo, hi, b, x0, 2)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.from_numpy(x0.copy()).to(dev)
+    R.symm_kacz(s, bd, xd, 2)
+    torch.cuda.synchronize()
+    got = xd.cpu().numpy()
+    err = np.max(np.abs(got - want))
+    assert err <= 1e-12 * (np.max(np.abs(want)) + np.max(np.abs(x0))), err
+    with pytest.raises(R.RaceError):
+        R.symm_kacz(s, bd, bd, 1)

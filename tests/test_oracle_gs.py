@@ -143,3 +143,66 @@ def test_spd_error_falls_in_the_energy_norm(oracle_mod, matgen_mod):
         assert en < prev
         prev = en
     assert np.linalg.norm(A @ x - b) < 1e-6 * np.linalg.norm(b)
+
+
+# ------------------------------------------------------------- symmetric Kaczmarz
+# A Kaczmarz pass in a row order is a Gauss-Seidel pass on A A^T y = b - A x0
+# with x = x0 + A^T y (the rows' projections written in the dual variables),
+# a textbook identity independent of the oracle's row loop.
+
+def kaczmarz_pass(A, b, x0, order):
+    M = A @ A.T
+    y = forward_pass(M, b - A @ x0, np.zeros(len(b)), order)
+    return x0 + A.T @ y
+
+
+@pytest.mark.parametrize("name,mk,nt,kw", [
+    ("natural", lambda g: g.stencil3d(5, npt=27, seed=3), 1, {"max_depth": 0}),
+    ("anderson6", lambda g: g.anderson(6, seed=2), 12, {}),
+    ("st27_6_d1", lambda g: g.stencil3d(6, npt=27, seed=5), 16, {"max_depth": 1}),
+])
+def test_kaczmarz_is_gauss_seidel_on_the_row_gram_matrix(oracle_mod, matgen_mod, name, mk, nt, kw):
+    m = mk(matgen_mod)
+    r, full = schedule_full(oracle_mod, m, nt, **kw)
+    A = dense_full(full)
+    n = m["n"]
+    rng = np.random.default_rng(8)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    fwd, bwd = execution_orders(r.stage_ptr, r.leaf_lo, r.leaf_hi)
+    want = kaczmarz_pass(A, b, x0, fwd)
+    want = kaczmarz_pass(A, b, want, bwd)
+    got = oracle_mod.symm_kacz(full, r.stage_ptr, r.leaf_lo, r.leaf_hi, b, x0, 1)
+    assert np.max(np.abs(got - want)) <= 1e-11 * (np.max(np.abs(want)) + 1.0)
+
+
+def test_kaczmarz_never_moves_away_from_the_solution(oracle_mod, matgen_mod):
+    """Each row projection is an orthogonal projection onto a hyperplane that
+    contains the solution, so ||x - x*|| cannot grow (any nonsingular A)."""
+    m = matgen_mod.anderson(7, seed=3)
+    r, full = schedule_full(oracle_mod, m, 16)
+    A = dense_full(full)
+    n = m["n"]
+    xs = np.random.default_rng(2).uniform(-1, 1, n)
+    b = A @ xs
+    x = np.zeros(n)
+    prev = np.linalg.norm(x - xs)
+    for _ in range(8):
+        x = oracle_mod.symm_kacz(full, r.stage_ptr, r.leaf_lo, r.leaf_hi, b, x, 1)
+        cur = np.linalg.norm(x - xs)
+        assert cur < prev
+        prev = cur
+
+
+def test_kaczmarz_leaf_order_and_planted_conflict(oracle_mod, matgen_mod):
+    m = matgen_mod.anderson(8, seed=4)
+    r, full = schedule_full(oracle_mod, m, 12)
+    n = m["n"]
+    rng = np.random.default_rng(6)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    x1 = oracle_mod.symm_kacz(full, r.stage_ptr, r.leaf_lo, r.leaf_hi, b, x0, 2)
+    lo2, hi2 = reverse_leaves_in_phases(r.stage_ptr, r.leaf_lo, r.leaf_hi)
+    assert np.array_equal(x1, oracle_mod.symm_kacz(full, r.stage_ptr, lo2, hi2, b, x0, 2))
+    one = np.array([0, len(r.leaf_lo)], np.int32)
+    lo3, hi3 = reverse_leaves_in_phases(one, r.leaf_lo, r.leaf_hi)
+    assert not np.array_equal(oracle_mod.symm_kacz(full, one, r.leaf_lo, r.leaf_hi, b, x0, 1),
+                              oracle_mod.symm_kacz(full, one, lo3, hi3, b, x0, 1))
