@@ -321,8 +321,10 @@ int symm_gs(const race_schedule *s, const double *b_d, double *x_d, int32_t swee
  * f = (b_i - sum_j a_ij x_j) / sum_j a_ij^2, x_j += f a_ij for every stored
  * column j of the row.  A row update writes x at all its columns, so
  * concurrent leaves must share no column: the schedule's distance-2
- * independence.  Arguments, layout and errors as for symm_gs; a zero row
- * gives inf or nan entries.                                                */
+ * independence, checked once per schedule on the host (schedules built with
+ * RACE_FLAG_ONE_LEVEL_STAGE0 are write-disjoint for half storage only and
+ * are refused with RACE_ERR_UNSUPPORTED).  Otherwise arguments, layout and
+ * errors as for symm_gs; a zero row gives inf or nan entries.              */
 int symm_kacz(const race_schedule *s, const double *b_d, double *x_d, int32_t sweeps, void *stream);
 
 /* Build and upload the full CRS used by spmv_full now (optional).          */

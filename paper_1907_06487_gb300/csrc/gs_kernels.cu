@@ -25,6 +25,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "race_internal.h"
 
@@ -114,6 +115,48 @@ void sweep_vt(const race_schedule* s, const double* b, double* x, int32_t sweeps
     }
 }
 
+// True when no two leaves of one phase hold rows at distance <= 2, i.e. the
+// closed neighbourhoods of their rows (the entries of x a Kaczmarz update
+// writes) are disjoint.  Schedules with one-level stage-0 groups are
+// write-disjoint for half storage only and fail this.
+bool kacz_independent(const race_schedule* s) {
+    const int32_t n = s->plan.n;
+    const auto& rp = s->h_rp;
+    const auto& col = s->h_col;
+    std::vector<int64_t> off(static_cast<size_t>(n) + 1, 0);
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = rp[r]; t < rp[r + 1]; ++t)
+            if (col[t] != r) {
+                ++off[r + 1];
+                ++off[col[t] + 1];
+            }
+    for (int32_t r = 0; r < n; ++r) off[r + 1] += off[r];
+    std::vector<int32_t> nbr(static_cast<size_t>(off[n]));
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = rp[r]; t < rp[r + 1]; ++t)
+            if (col[t] != r) {
+                nbr[fill[r]++] = col[t];
+                nbr[fill[col[t]]++] = r;
+            }
+    std::vector<int32_t> owner(static_cast<size_t>(n), -1), phase(static_cast<size_t>(n), -1);
+    const auto& sp = s->plan.stage_ptr;
+    auto claim = [&](int32_t c, int32_t ph, int32_t q) {
+        if (phase[c] == ph && owner[c] != q) return false;
+        phase[c] = ph;
+        owner[c] = q;
+        return true;
+    };
+    for (size_t ph = 0; ph + 1 < sp.size(); ++ph)
+        for (int32_t q = sp[ph]; q < sp[ph + 1]; ++q)
+            for (int32_t r = s->plan.leaf_lo[q]; r < s->plan.leaf_hi[q]; ++r) {
+                if (!claim(r, static_cast<int32_t>(ph), q)) return false;
+                for (int64_t e = off[r]; e < off[r + 1]; ++e)
+                    if (!claim(nbr[e], static_cast<int32_t>(ph), q)) return false;
+            }
+    return true;
+}
+
 template <bool KACZ>
 int run(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, void* stream, const char* name) {
     if (!s || !b_d || !x_d) {
@@ -131,6 +174,14 @@ int run(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, 
     if (sweeps < 0) {
         race_set_detail("sweeps < 0");
         return RACE_ERR_INVALID;
+    }
+    if (KACZ) {
+        if (s->kacz_state == 0) s->kacz_state = kacz_independent(s) ? 1 : -1;
+        if (s->kacz_state < 0) {
+            race_set_detail("the schedule's phases are not distance-2 independent on the full rows "
+                            "(RACE_FLAG_ONE_LEVEL_STAGE0): a Kaczmarz update writes every column of its row");
+            return RACE_ERR_UNSUPPORTED;
+        }
     }
     if (!s->d_frp) {
         const int rc = race_prepare_full(const_cast<race_schedule*>(s), stream);

@@ -145,6 +145,9 @@ struct race_schedule {
     mutable SellSet sell;  // built on first use of RACE_EXEC_SELL_DF64
     race_launch launch{};       // symm_spmv executor and shape
     race_launch full_launch{};  // spmv_full shape
+    // symm_kacz: phases checked on first use for distance-2 independence on
+    // the full rows (0 = not checked, 1 = independent, -1 = not)
+    mutable int32_t kacz_state = 0;
 };
 
 // Row blocks for the streaming kernels: consecutive rows with at most

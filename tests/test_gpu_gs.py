@@ -86,7 +86,9 @@ def test_symm_gs_edges(dev, matgen_mod):
     assert e.value.code == R.RACE_ERR_UNSUPPORTED
 
 
-KACZ_CASES = CASES + [("anderson12", lambda g: g.anderson(12, seed=1), 48, {})]
+# Kaczmarz writes every column of a row: the one-level stage-0 schedule
+# (write-disjoint for half storage only) is refused instead (below)
+KACZ_CASES = [c for c in CASES if "one_level" not in c[0]] + [("anderson12", lambda g: g.anderson(12, seed=1), 48, {})]
 
 
 @pytest.mark.parametrize("name,mk,nt,kw", KACZ_CASES, ids=[c[0] for c in KACZ_CASES])
@@ -111,3 +113,16 @@ def test_symm_kacz_parity(dev, oracle_mod, matgen_mod, name, mk, nt, kw):
     assert err <= 1e-12 * (np.max(np.abs(want)) + np.max(np.abs(x0))), err
     with pytest.raises(R.RaceError):
         R.symm_kacz(s, bd, bd, 1)
+
+
+def test_symm_kacz_refuses_one_level_stage0(dev, matgen_mod):
+    m = matgen_mod.stencil3d(16, npt=27, seed=4)
+    s = R.race_build(m, 48, max_depth=1, one_level_stage0=True)
+    b = torch.ones(m["n"], dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    with pytest.raises(R.RaceError) as e:
+        R.symm_kacz(s, b, x, 1)
+    assert e.value.code == R.RACE_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert torch.all(x == 0.0)  # nothing ran
+    R.symm_gs(s, b, x, 1)  # Gauss-Seidel needs distance 1 only: accepted
