@@ -177,9 +177,15 @@ int race_build(const race_csr_upper *a, const race_params *p, void *stream, race
 int race_upload(race_schedule *s, void *stream);
 
 /* symm_spmv — b = A x for the symmetric A whose upper triangle was given,
- * i.e. b = A_u x + A_u^T x - diag(A) x (Alg. "SymmSpMV"), run phase by
- * phase on the device so that no two concurrent workers write the same
- * entry of b.  x, b: device arrays of n doubles in permuted order.        */
+ * i.e. b = A_u x + A_u^T x - diag(A) x (Alg. "SymmSpMV"), with the
+ * schedule's current executor (race_set_launch; RACE_EXEC_LEAF_GROUP after
+ * race_build).  The leaf executors (RACE_EXEC_LEAF_GROUP, _LEAF_CTA,
+ * _WINDOW_RACE) run the schedule phase by phase, so that no two concurrent
+ * leaves write the same entry of b; the row-parallel executors (_ATOMIC,
+ * _ROWS_RED, _STREAM_RED, _PIPE_RED, _WINDOW_RED, _DF64_RED, _SELL_DF64,
+ * _STAGED) run all rows at once on the schedule's permuted matrix and
+ * resolve the concurrent writes to b by reductions at L2.  x, b: device
+ * arrays of n doubles in permuted order.                                  */
 int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stream);
 
 /* Executors of SymmSpMV (symm_spmv_exec).                                  */
@@ -243,6 +249,27 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    copy (about the matrix's size again);
                                    regs_per_row = entries per lane and step
                                    (4, 8 or 16).                            */
+#define RACE_EXEC_STAGED 10     /* as ROWS_RED with one row per lane: warp
+                                   tiles of 32 consecutive rows whose stored
+                                   values and columns are copied into shared
+                                   memory by the bulk-copy (TMA) engine, two
+                                   stages per warp so the next tile's copy
+                                   overlaps the current tile's work; x
+                                   gathered, the transposed update and the
+                                   row sums reductions at L2.  Per quarter of
+                                   the warps the row sums run in FP64 or in
+                                   double-float arithmetic
+                                   (rowsum_fp64_quarters) and the transposed
+                                   products likewise (fp64_quarters); the
+                                   result stays within 1e-12 sum_j
+                                   |a_ij x_j| of the exact one.  Entries
+                                   whose value or x lies outside
+                                   [2^-50, 2^51) in magnitude (zero excepted)
+                                   and rows of more than 64 entries are taken
+                                   in FP64.  regs_per_row: entries per lane
+                                   and step (4, or 8 when >= 8).  Needs no
+                                   preparation and no memory beyond the
+                                   schedule's.                              */
 
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {
@@ -262,6 +289,10 @@ typedef struct {
                                 transposed updates use FP64 multiplies, in
                                 the rest double-float arithmetic; shares the
                                 work between the FP64 and integer pipes  */
+    int32_t rowsum_fp64_quarters; /* RACE_EXEC_STAGED: in this many quarters
+                                of the warps (0..4) the row sums are FP64
+                                multiply-adds, in the rest double-float
+                                arithmetic (other executors: always FP64) */
 } race_launch;
 
 /* race_set_launch / race_get_launch — which = 0: symm_spmv, which = 1:
@@ -284,6 +315,19 @@ int race_probe_scatter(const race_schedule *s, int32_t mode, double *b_d, void *
  * (and clears it) if a bounded device wait of this schedule's kernels gave
  * up since the last poll, else RACE_OK.                                    */
 int race_poll_status(race_schedule *s, void *stream);
+
+/* race_probe_wait_timeout — diagnostic of the bounded device waits,
+ * computes nothing usable: runs the RACE_EXEC_STAGED kernel on x_d / b_d
+ * (device arrays of n doubles, not aliasing; b_d is left undefined) with
+ * every stage's mbarrier expecting 16 bytes more than its copies deliver
+ * and a spin limit of 4096 polls, so every wait gives up while none of the
+ * copies is left in flight.  The kernel records RACE_ERR_TIMEOUT in the
+ * schedule's status word: race_poll_status then returns it once and clears
+ * it.  No device fault, trap or endless wait is involved.  The paper has no
+ * counterpart (failure detection of this library's own kernels).
+ * Errors: RACE_ERR_INVALID (NULL, aliasing), _UNSUPPORTED (host-only
+ * schedule), _CUDA.                                                        */
+int race_probe_wait_timeout(const race_schedule *s, const double *x_d, double *b_d, void *stream);
 
 /* symm_spmv_exec — symm_spmv with an explicit executor (RACE_EXEC_*).
  * Same arguments, layout and errors as symm_spmv.                          */
@@ -453,10 +497,15 @@ int race_mlp_adam(float *params_d, const float *grad_d, float *m_d, float *v_d, 
  * (RACE_EXEC_STREAM_RED) that needs no schedule handle.
  *
  * Arguments (all device pointers owned by the caller): an upper-triangle
- * CRS with n rows and nnz stored entries -- row_ptr_d (n+1, row_ptr[0] = 0),
- * col_d and val_d (nnz, FP64), each row's columns >= the row index; any
- * row order the caller chooses (e.g. a schedule's permuted matrix);
- * x_d (n) and b_d (n), not aliasing.  b is overwritten.
+ * CRS with n rows and nnz stored entries -- row_ptr_d (n+1, row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz; checked on the device before anything
+ * is computed), col_d and val_d (nnz, FP64), each row's columns in [row, n)
+ * (not checked: that would cost a pass over col); any row order the caller
+ * chooses (e.g. a schedule's permuted matrix); x_d (n) and b_d (n), not
+ * aliasing.  row_ptr_d, col_d and val_d must start at 16-byte boundaries
+ * (the kernel stages them with bulk copies; cudaMalloc and torch give 256).
+ * b is overwritten; when the call is refused (any error code below but
+ * _CUDA and _TIMEOUT) b is left untouched.
  *
  * Scratch: the kernel's row-block table and status word live in a fixed
  * device array of about 3.4 MB that every GPU loading the library holds
@@ -471,8 +520,9 @@ int race_mlp_adam(float *params_d, const float *grad_d, float *m_d, float *v_d, 
  * streams or threads) race with each other: serialise them.  The call
  * enqueues its work on `stream` and waits for that stream twice (to size the
  * launch and to read the status), so it returns only when b is complete.
- * Errors: RACE_ERR_INVALID, _OVERFLOW, _UNSUPPORTED, _CUDA, _TIMEOUT; on an
- * error b is undefined.                                                    */
+ * Errors: RACE_ERR_INVALID (n < 1, nnz < n, NULL, aliasing, misaligned
+ * arrays, malformed row_ptr), _OVERFLOW, _UNSUPPORTED, _CUDA, _TIMEOUT; after
+ * _CUDA or _TIMEOUT b is undefined.                                        */
 int symm_spmv_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr_d, const int32_t *col_d, const double *val_d,
                       const double *x_d, double *b_d, void *stream);
 

@@ -49,7 +49,8 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_last_error_detail", "race_set_launch", "race_get_launch", "race_poll_status", "race_probe_scatter",
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
-            "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz")
+            "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz",
+            "race_probe_wait_timeout")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -61,12 +62,13 @@ RACE_EXEC_WINDOW_RED = 6
 RACE_EXEC_WINDOW_RACE = 7
 RACE_EXEC_DF64_RED = 8
 RACE_EXEC_SELL_DF64 = 9
+RACE_EXEC_STAGED = 10
 
 
 class race_launch(ctypes.Structure):
     _fields_ = [("executor", ctypes.c_int32), ("group_lanes", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("regs_per_row", ctypes.c_int32),
-                ("fp64_quarters", ctypes.c_int32)]
+                ("fp64_quarters", ctypes.c_int32), ("rowsum_fp64_quarters", ctypes.c_int32)]
 
 
 class RaceError(RuntimeError):
@@ -141,6 +143,8 @@ def lib():
     L.race_probe_scatter.restype = ctypes.c_int
     L.race_poll_status.argtypes = [vp, vp]
     L.race_poll_status.restype = ctypes.c_int
+    L.race_probe_wait_timeout.argtypes = [vp, vp, vp, vp]
+    L.race_probe_wait_timeout.restype = ctypes.c_int
     L.symm_spmv_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     L.symm_spmv_noalloc.restype = ctypes.c_int
     pvp = ctypes.POINTER(vp)
@@ -337,10 +341,10 @@ def symm_kacz(s: Schedule, b, x, sweeps=1, stream=None):
 
 
 def race_set_launch(s: Schedule, which, executor=0, group_lanes=8, rows_per_group=4, blocks_per_sm=0,
-                    regs_per_row=8, fp64_quarters=0):
+                    regs_per_row=8, fp64_quarters=0, rowsum_fp64_quarters=4):
     """which = 0: symm_spmv, 1: spmv_full."""
     lc = race_launch(int(executor), int(group_lanes), int(rows_per_group), int(blocks_per_sm), int(regs_per_row),
-                     int(fp64_quarters))
+                     int(fp64_quarters), int(rowsum_fp64_quarters))
     _check(lib().race_set_launch(s.handle, int(which), ctypes.byref(lc)), "race_set_launch")
 
 
@@ -357,6 +361,12 @@ def race_probe_scatter(s: Schedule, mode, b, stream=None):
 
 def race_poll_status(s: Schedule, stream=None):
     _check(lib().race_poll_status(s.handle, _stream(stream)), "race_poll_status")
+
+
+def race_probe_wait_timeout(s: Schedule, x, b, stream=None):
+    """Diagnostic: run the staged kernel with waits that give up (b undefined);
+    the next race_poll_status then raises RACE_ERR_TIMEOUT once."""
+    _check(lib().race_probe_wait_timeout(s.handle, _ptr(x), _ptr(b), _stream(stream)), "race_probe_wait_timeout")
 
 
 class Batch:

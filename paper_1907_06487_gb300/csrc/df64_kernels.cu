@@ -44,29 +44,15 @@ __device__ __forceinline__ unsigned lane_mask() {
     }
 }
 
-__device__ __forceinline__ bool out_of_range(double v) {
+__host__ __device__ __forceinline__ bool out_of_range(double v) {
     float h, l;
     return df64::split(v, h, l) != 0;
 }
-__device__ __forceinline__ bool out_of_range(float v) {
-    const uint32_t u = __float_as_uint(v);
+__host__ __device__ __forceinline__ bool out_of_range(float v) {
+    const uint32_t u = df64::f2u(v);
     const int e = static_cast<int>((u >> 23) & 0xFFu) - 127;
     return (u << 1) != 0 && (e < df64::kEmin || e > df64::kEmax);
 }
-
-// Sets *bad when a stored off-diagonal value is nonzero and outside the
-// split's range (one thread per row).
-template <typename VT>
-__global__ void k_check_offdiag(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                const VT* __restrict__ val, int32_t* bad) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
-        const int32_t hi = __ldg(rp + r + 1);
-        for (int32_t j = __ldg(rp + r); j < hi; ++j)
-            if (__ldg(col + j) != r && out_of_range(__ldg(val + j))) *bad = 1;
-    }
-}
-
 
 // How a row scatters its transposed part.
 enum Scatter { kSplit = 0, kFp64 = 1, kNone = 2 };
@@ -143,16 +129,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
     }
 }
 
-int sm_count_of_device() {
-    static int count = 0;
-    if (count == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
-        if (count <= 0) count = 1;
-    }
-    return count;
-}
+int sm_count_of_device() { return race_device_sms(); }
 
 template <typename VT, int G>
 void launch_g(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
@@ -184,32 +161,24 @@ void launch_vt(const race_schedule* s, int G, const double* x, double* b, cudaSt
 }  // namespace
 
 int race_df64_prepare(const race_schedule* s) {
-    if (s->df64_state == 1) return RACE_OK;
-    if (s->df64_state == -1) {
-        race_set_detail("an off-diagonal value outside the double-float magnitude range [2^-50, 2^51)");
-        return RACE_ERR_UNSUPPORTED;
+    int32_t st = s->df64_state.load(std::memory_order_acquire);
+    if (st == 0) {
+        // one pass over the host copy of the permuted matrix (threads that
+        // race here compute the same answer)
+        bool bad = false;
+        const int32_t n = s->plan.n;
+        for (int32_t r = 0; r < n && !bad; ++r)
+            for (int32_t j = s->h_rp[r]; j < s->h_rp[r + 1]; ++j) {
+                if (s->h_col[j] == r) continue;
+                if (s->val_type == RACE_F64 ? out_of_range(s->h_val64[j]) : out_of_range(s->h_val32[j])) {
+                    bad = true;
+                    break;
+                }
+            }
+        st = bad ? -1 : 1;
+        s->df64_state.store(st, std::memory_order_release);
     }
-    const int32_t n = s->plan.n;
-    int32_t* d_bad = nullptr;
-    cudaError_t e = cudaMalloc(&d_bad, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int32_t));
-    const int grid = sm_count_of_device() * 8;
-    if (e == cudaSuccess && n > 0) {
-        if (s->val_type == RACE_F64)
-            k_check_offdiag<double><<<grid, kBlock>>>(n, s->d_rp, s->d_col, static_cast<const double*>(s->d_val), d_bad);
-        else
-            k_check_offdiag<float><<<grid, kBlock>>>(n, s->d_rp, s->d_col, static_cast<const float*>(s->d_val), d_bad);
-        e = cudaGetLastError();
-    }
-    int32_t bad = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (d_bad) cudaFree(d_bad);
-    if (e != cudaSuccess) {
-        race_set_detail(std::string("double-float range check: ") + cudaGetErrorString(e));
-        return RACE_ERR_CUDA;
-    }
-    s->df64_state = bad ? -1 : 1;
-    if (bad) {
+    if (st == -1) {
         race_set_detail("an off-diagonal value outside the double-float magnitude range [2^-50, 2^51)");
         return RACE_ERR_UNSUPPORTED;
     }

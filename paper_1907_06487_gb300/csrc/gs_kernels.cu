@@ -176,8 +176,12 @@ int run(const race_schedule* s, const double* b_d, double* x_d, int32_t sweeps, 
         return RACE_ERR_INVALID;
     }
     if (KACZ) {
-        if (s->kacz_state == 0) s->kacz_state = kacz_independent(s) ? 1 : -1;
-        if (s->kacz_state < 0) {
+        int32_t ks = s->kacz_state.load(std::memory_order_acquire);
+        if (ks == 0) {
+            ks = kacz_independent(s) ? 1 : -1;  // threads that race here compute the same answer
+            s->kacz_state.store(ks, std::memory_order_release);
+        }
+        if (ks < 0) {
             race_set_detail("the schedule's phases are not distance-2 independent on the full rows "
                             "(RACE_FLAG_ONE_LEVEL_STAGE0): a Kaczmarz update writes every column of its row");
             return RACE_ERR_UNSUPPORTED;

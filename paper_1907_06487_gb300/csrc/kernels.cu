@@ -624,16 +624,7 @@ __global__ void k_permute(int32_t n, int32_t k, const int32_t* __restrict__ perm
     }
 }
 
-int g_sm_count = 0;
-int sm_count() {
-    if (g_sm_count == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sm_count <= 0) g_sm_count = 1;
-    }
-    return g_sm_count;
-}
+int sm_count() { return race_device_sms(); }
 
 int grid_for(int64_t threads_needed, int blocks_per_sm = 0) {
     const int64_t per_sm = blocks_per_sm > 0 ? blocks_per_sm : (2048 / kBlock);
@@ -728,7 +719,7 @@ void launch_atomic(const race_schedule* s, const double* x, double* b, cudaStrea
 }
 
 template <typename VT>
-void launch_symm_exec(const race_schedule* s, int exec, const double* x, double* b, cudaStream_t st) {
+int launch_symm_exec(const race_schedule* s, int exec, const double* x, double* b, cudaStream_t st) {
 #define RACE_DISPATCH(FN)                          \
     switch (s->group_lanes) {                      \
         case 4: FN<VT, 4>(s, x, b, st); break;     \
@@ -745,7 +736,8 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
     } else if (exec == RACE_EXEC_ROWS_RED || (exec == RACE_EXEC_STREAM_RED && s->max_row_upper > 1024)) {
         RACE_GU_SWITCH(launch_rows_red_gu, VT, s->launch.group_lanes, s->launch.rows_per_group, s, x, b, st);
     } else if (exec == RACE_EXEC_STREAM_RED) {
-        race_stream_symm_red(s, x, b, st, sm_count());
+        const int rc = race_stream_symm_red(s, x, b, st, sm_count());
+        if (rc) return rc;
     } else if (exec == RACE_EXEC_PIPE_RED) {
         launch_pipe<VT, true>(s->plan.n, s->d_rp, s->d_col, s->d_val, x, b, s->launch, st);
     } else if (exec == RACE_EXEC_WINDOW_RED || exec == RACE_EXEC_WINDOW_RACE) {
@@ -758,6 +750,7 @@ void launch_symm_exec(const race_schedule* s, int exec, const double* x, double*
         RACE_DISPATCH(launch_phases)
     }
 #undef RACE_DISPATCH
+    return RACE_OK;
 }
 
 template <typename VT>
@@ -879,15 +872,17 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
     }
     if (s->launch.executor == RACE_EXEC_DF64_RED) return race_df64_launch(s, x_d, b_d, st);
     if (s->launch.executor == RACE_EXEC_SELL_DF64) return race_sell_launch(s, x_d, b_d, st);
-    if (s->val_type == RACE_F64) launch_symm_exec<double>(s, s->launch.executor, x_d, b_d, st);
-    else launch_symm_exec<float>(s, s->launch.executor, x_d, b_d, st);
+    if (s->launch.executor == RACE_EXEC_STAGED) return race_staged_launch(s, s->launch, x_d, b_d, st, kStagedSpinLimit, 0);
+    rc = s->val_type == RACE_F64 ? launch_symm_exec<double>(s, s->launch.executor, x_d, b_d, st)
+                                 : launch_symm_exec<float>(s, s->launch.executor, x_d, b_d, st);
+    if (rc) return rc;
     return check_launch("symm_spmv");
 }
 
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_SELL_DF64) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_STAGED) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -899,8 +894,10 @@ int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, 
     }
     if (executor == RACE_EXEC_DF64_RED) return race_df64_launch(s, x_d, b_d, st);
     if (executor == RACE_EXEC_SELL_DF64) return race_sell_launch(s, x_d, b_d, st);
-    if (s->val_type == RACE_F64) launch_symm_exec<double>(s, executor, x_d, b_d, st);
-    else launch_symm_exec<float>(s, executor, x_d, b_d, st);
+    if (executor == RACE_EXEC_STAGED) return race_staged_launch(s, s->launch, x_d, b_d, st, kStagedSpinLimit, 0);
+    rc = s->val_type == RACE_F64 ? launch_symm_exec<double>(s, executor, x_d, b_d, st)
+                                 : launch_symm_exec<float>(s, executor, x_d, b_d, st);
+    if (rc) return rc;
     return check_launch("symm_spmv_exec");
 }
 
@@ -933,9 +930,10 @@ int spmv_full(const race_schedule* s, const double* x_d, double* b_d, void* stre
         if (rc) return rc;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s->full_launch.executor == 1 && s->max_row_full <= 1024)
-        race_stream_full(s, x_d, b_d, st, sm_count());
-    else if (s->full_launch.executor == 2 && s->val_type == RACE_F64)
+    if (s->full_launch.executor == 1 && s->max_row_full <= 1024) {
+        rc = race_stream_full(s, x_d, b_d, st, sm_count());
+        if (rc) return rc;
+    } else if (s->full_launch.executor == 2 && s->val_type == RACE_F64)
         launch_pipe<double, false>(s->plan.n, s->d_frp, s->d_fcol, s->d_fval, x_d, b_d, s->full_launch, st);
     else if (s->full_launch.executor == 2)
         launch_pipe<float, false>(s->plan.n, s->d_frp, s->d_fcol, s->d_fval, x_d, b_d, s->full_launch, st);
@@ -954,8 +952,9 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool g_ok = l->group_lanes == 1 || l->group_lanes == 2 || l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
-        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_SELL_DF64 || l->regs_per_row < 0 ||
-        l->regs_per_row > 16 || l->fp64_quarters < 0 || l->fp64_quarters > 4 || (which != 0 && which != 1)) {
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_STAGED || l->regs_per_row < 0 ||
+        l->regs_per_row > 16 || l->fp64_quarters < 0 || l->fp64_quarters > 4 || l->rowsum_fp64_quarters < 0 ||
+        l->rowsum_fp64_quarters > 4 || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
     }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -33,7 +34,7 @@ void release_device(race_schedule* s) {
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
-    s->df64_state = 0;
+    s->df64_state.store(0);
     race_free_sell(s->sell);
     for (WindowSet* w : {&s->win_red, &s->win_race}) {
         void* wp[] = {w->d_hdr, w->d_ext, w->d_val, w->d_lidx, w->d_pos, w->d_slot_row, w->d_rs_pos,
@@ -147,6 +148,26 @@ int pick_lanes(int64_t nnz, int32_t n) {
 }  // namespace
 
 void race_set_detail(const std::string& s) { g_detail = s; }
+
+int race_device_sms() {
+    // one slot per device ordinal; 0 = not looked up yet (a race between two
+    // threads stores the same value twice)
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev >= 64) {
+        int c = 0;
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return c > 0 ? c : 1;
+    }
+    int c = cache[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        if (c <= 0) c = 1;
+        cache[dev].store(c, std::memory_order_relaxed);
+    }
+    return c;
+}
 
 std::vector<int32_t> race_row_blocks(const int32_t* rp, int32_t n, int32_t max_nnz, int32_t max_rows) {
     std::vector<int32_t> out(1, 0);

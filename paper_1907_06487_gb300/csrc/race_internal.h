@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -141,13 +142,13 @@ struct race_schedule {
     WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
     // double-float executor: off-diagonal values range-checked on first use
     // (0 = not checked, 1 = ready, -1 = a value out of range)
-    mutable int32_t df64_state = 0;
+    mutable std::atomic<int32_t> df64_state{0};
     mutable SellSet sell;  // built on first use of RACE_EXEC_SELL_DF64
     race_launch launch{};       // symm_spmv executor and shape
     race_launch full_launch{};  // spmv_full shape
     // symm_kacz: phases checked on first use for distance-2 independence on
     // the full rows (0 = not checked, 1 = independent, -1 = not)
-    mutable int32_t kacz_state = 0;
+    mutable std::atomic<int32_t> kacz_state{0};
 };
 
 // Row blocks for the streaming kernels: consecutive rows with at most
@@ -166,7 +167,8 @@ int race_window_launch(const race_schedule* s, bool race_mode, const double* x, 
                        int sm_count);
 
 // Double-float executor (df64_kernels.cu): preparation (range check of the
-// off-diagonal values) and the launch, which prepares on first use.
+// off-diagonal values on the host copy of the matrix, once per schedule; no
+// device work) and the launch, which prepares on first use.
 int race_df64_prepare(const race_schedule* s);
 int race_df64_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
 
@@ -177,6 +179,17 @@ void race_make_sell(int32_t n, const int32_t* rp, const int32_t* col, const doub
 int race_sell_prepare(const race_schedule* s);
 void race_free_sell(SellSet& q);
 int race_sell_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
+
+// Warp-tile staged executor (staged_kernels.cu).  spin_limit bounds every
+// mbarrier wait (polls); extra_tx is added to every stage's expected byte
+// count (0 in production; the timeout probe overstates it so that every wait
+// gives up while no copy stays in flight).
+constexpr uint32_t kStagedSpinLimit = 1u << 26;
+int race_staged_launch(const race_schedule* s, const race_launch& l, const double* x, double* b, cudaStream_t st,
+                       uint32_t spin_limit, uint32_t extra_tx);
+
+// Multiprocessor count of the current device (cached per device).
+int race_device_sms();
 
 // Error detail for race_last_error_detail (thread-local).
 void race_set_detail(const std::string& s);

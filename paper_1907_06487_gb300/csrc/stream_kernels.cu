@@ -140,11 +140,13 @@ __global__ void __launch_bounds__(kThreads) k_stream(int64_t nblk, const int32_t
 template <typename VT, int MODE>
 int launch_stream(int64_t nblk, const int32_t* blk_row, const int32_t* rp, const int32_t* col, const VT* val,
                   const double* x, double* b, int32_t* status, int sm_count, int ctas_per_sm, cudaStream_t st) {
-    static bool configured = false;
+    // set on every launch: the attribute is per device, and the call is cheap
     const size_t smem = stream_smem_bytes<VT>();
-    if (!configured) {
+    const cudaError_t e =
         cudaFuncSetAttribute(k_stream<VT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        configured = true;
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("k_stream: shared-memory attribute: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
     }
     if (nblk <= 0) return RACE_OK;
     const int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 4;
@@ -198,7 +200,7 @@ constexpr int64_t kMaxNnz = int64_t(1) << 28;     // stored upper entries
 constexpr int kGroupRows = 256;                   // rows per counting group
 constexpr int64_t kMaxGroups = kMaxRows / kGroupRows;
 constexpr int64_t kMaxBlocks = kMaxRows / 64 + kMaxNnz / 512 + 2;
-constexpr int64_t kHeader = 64;                   // [0] status [1] blocks [2] first unsafe [3] long row
+constexpr int64_t kHeader = 64;  // [0] status [1] blocks [2] first unsafe [3] long row [4] bad row_ptr
 constexpr int64_t kWords = kHeader + kMaxGroups + kMaxBlocks + 1;   // 3.4 MB in total
 
 static __device__ __align__(256) int32_t g_scratch[kWords];
@@ -213,26 +215,36 @@ __global__ void k_reset(int32_t* sc) {
         sc[1] = 0;
         sc[2] = INT32_MAX;
         sc[3] = 0;
+        sc[4] = 0;
     }
 }
 
 // per 256-row group: number of block starts (one warp per group); flags any
-// row longer than 512 entries
-__global__ void k_count(int32_t n, const int32_t* __restrict__ rp, int32_t* sc) {
+// row longer than 512 entries (sc[3]) and row pointers that decrease, do not
+// start at 0 or do not end at nnz (sc[4]); the block table is used only when
+// neither flag is set
+__global__ void k_count(int32_t n, int64_t nnz, const int32_t* __restrict__ rp, int32_t* sc) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int64_t ngroups = (static_cast<int64_t>(n) + kGroupRows - 1) / kGroupRows;
     for (int64_t g = warp; g < ngroups; g += nwarps) {
         int32_t cnt = 0;
-        bool longrow = false;
+        bool longrow = false, bad = false;
         for (int k = 0; k < kGroupRows / 32; ++k) {
             const int64_t r = g * kGroupRows + k * 32 + lane;
             const bool f = r < n && starts_block(rp, r);
-            longrow |= r < n && (__ldg(rp + r + 1) - __ldg(rp + r)) > 512;
+            if (r < n) {
+                const int64_t len = static_cast<int64_t>(__ldg(rp + r + 1)) - __ldg(rp + r);
+                longrow |= len > 512;
+                bad |= len < 0;
+                if (r == 0) bad |= __ldg(rp) != 0;
+                if (r == n - 1) bad |= static_cast<int64_t>(__ldg(rp + n)) != nnz;
+            }
             cnt += __popc(__ballot_sync(0xffffffffu, f));
         }
         if (__any_sync(0xffffffffu, longrow) && lane == 0) atomicExch(sc + 3, 1);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(sc + 4, 1);
         if (lane == 0) sc[kHeader + g] = cnt;
     }
 }
@@ -265,6 +277,9 @@ __global__ void __launch_bounds__(1024) k_scan(int32_t ngroups, int32_t* sc) {
 
 // block starts in row order, then the sentinel n
 __global__ void k_write(int32_t n, const int32_t* __restrict__ rp, int32_t* sc) {
+    // malformed row pointers (flagged by k_count, which ran before on the same
+    // stream) could give more block starts than the table holds: write none
+    if (sc[4] != 0 || sc[1] > kMaxBlocks) return;
     int32_t* tbl = sc + kHeader + kMaxGroups;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -286,6 +301,7 @@ __global__ void k_write(int32_t n, const int32_t* __restrict__ rp, int32_t* sc) 
 
 // first block whose widened copies would leave [0, nnz) or [0, n]
 __global__ void k_safe(int32_t n, int64_t nnz, const int32_t* __restrict__ rp, int32_t* sc) {
+    if (sc[4] != 0 || sc[1] > kMaxBlocks) return;
     const int32_t* tbl = sc + kHeader + kMaxGroups;
     const int32_t nb = sc[1];
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nb;
@@ -335,6 +351,12 @@ extern "C" int symm_spmv_noalloc(int32_t n, int64_t nnz, const int32_t* row_ptr_
         race_set_detail("symm_spmv_noalloc: x and b alias");
         return RACE_ERR_INVALID;
     }
+    if ((reinterpret_cast<uintptr_t>(row_ptr_d) | reinterpret_cast<uintptr_t>(col_d) |
+         reinterpret_cast<uintptr_t>(val_d)) & 15u) {
+        // the row blocks are staged by bulk copies, which start at 16-byte boundaries
+        race_set_detail("symm_spmv_noalloc: row_ptr, col and val must be 16-byte aligned");
+        return RACE_ERR_INVALID;
+    }
     if (n > kMaxRows || nnz > kMaxNnz) {
         race_set_detail("symm_spmv_noalloc: at most 16,777,216 rows and 268,435,456 stored entries "
                         "(fixed scratch of the non-allocating path)");
@@ -366,26 +388,31 @@ extern "C" int symm_spmv_noalloc(int32_t n, int64_t nnz, const int32_t* row_ptr_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int32_t ngroups = static_cast<int32_t>((static_cast<int64_t>(n) + kGroupRows - 1) / kGroupRows);
     const int gw = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(ngroups) * 32 + 255) / 256, g_sm[dev] * 8));
-    e = cudaMemsetAsync(b_d, 0, sizeof(double) * static_cast<size_t>(n), st);
-    if (e != cudaSuccess) {
-        race_set_detail(std::string("symm_spmv_noalloc: memset: ") + cudaGetErrorString(e));
-        return RACE_ERR_CUDA;
-    }
     k_reset<<<1, 32, 0, st>>>(sc);
-    k_count<<<gw, 256, 0, st>>>(n, row_ptr_d, sc);
+    k_count<<<gw, 256, 0, st>>>(n, nnz, row_ptr_d, sc);
     k_scan<<<1, 1024, 0, st>>>(ngroups, sc);
     k_write<<<gw, 256, 0, st>>>(n, row_ptr_d, sc);
     k_safe<<<g_sm[dev] * 4, 256, 0, st>>>(n, nnz, row_ptr_d, sc);
-    int32_t head[4] = {0, 0, 0, 0};
+    int32_t head[5] = {0, 0, 0, 0, 0};
     e = cudaMemcpyAsync(head, sc, sizeof(head), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         race_set_detail(std::string("symm_spmv_noalloc: ") + cudaGetErrorString(e));
         return RACE_ERR_CUDA;
     }
+    if (head[4]) {
+        race_set_detail("symm_spmv_noalloc: row_ptr decreases, row_ptr[0] != 0 or row_ptr[n] != nnz");
+        return RACE_ERR_INVALID;
+    }
     if (head[3]) {
         race_set_detail("symm_spmv_noalloc: a row has more than 512 stored entries");
         return RACE_ERR_UNSUPPORTED;
+    }
+    // b is written only once the request has been accepted
+    e = cudaMemsetAsync(b_d, 0, sizeof(double) * static_cast<size_t>(n), st);
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("symm_spmv_noalloc: memset: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
     }
     const int64_t n_safe = std::min(head[2], head[1]);
     const int32_t* tbl = sc + kHeader + kMaxGroups;

@@ -208,3 +208,25 @@ def test_full_size_schedules_match_oracle(oracle_mod, name):
     o = oracle_mod.Race(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], rcm=cfg.get("rcm", False))
     assert s.export() == o.export()
     s.free()
+
+
+def test_noalloc_refuses_before_touching_the_device(lib):
+    """symm_spmv_noalloc checks sizes, NULLs, aliasing and the 16-byte
+    alignment its bulk copies need on the host, before any CUDA call (so the
+    refusals need no GPU; the addresses below are never dereferenced)."""
+    A = 0x10000  # 16-byte aligned stand-in addresses
+    cases = [
+        ((0, 0, A, A, A, A, A + 0x100), R.RACE_ERR_INVALID),            # n < 1
+        ((8, 4, A, A, A, A, A + 0x100), R.RACE_ERR_INVALID),            # nnz < n
+        ((8, 8, A, A, A, A, A), R.RACE_ERR_INVALID),                     # x and b alias
+        ((8, 8, 0, A, A, A, A + 0x100), R.RACE_ERR_INVALID),             # NULL row_ptr
+        ((8, 8, A + 4, A, A, A, A + 0x100), R.RACE_ERR_INVALID),         # row_ptr 4 bytes off
+        ((8, 8, A, A + 8, A, A, A + 0x100), R.RACE_ERR_INVALID),         # col 8 bytes off
+        ((8, 8, A, A, A + 8, A, A + 0x100), R.RACE_ERR_INVALID),         # val 8 bytes off
+        (((1 << 24) + 1, (1 << 24) + 1, A, A, A, A, A + 0x100), R.RACE_ERR_OVERFLOW),
+        ((8, (1 << 28) + 1, A, A, A, A, A + 0x100), R.RACE_ERR_OVERFLOW),
+    ]
+    for args, code in cases:
+        with pytest.raises(R.RaceError) as e:
+            R.symm_spmv_noalloc(*args)
+        assert e.value.code == code, args
