@@ -1,13 +1,27 @@
 #!/usr/bin/env python
 """SymmSpMV benchmark on GB300 (one JSON line on stdout).
 
-Workload (default): the periodic Heisenberg XXZ chain L=26, Sz=0 sector
-(10,400,600 rows, 80,708,656 stored upper nonzeros, 151,016,712 full
+Headline workload (default): the periodic Heisenberg XXZ chain L=26, Sz=0
+sector (10,400,600 rows, 80,708,656 stored upper nonzeros, 151,016,712 full
 nonzeros), FP64 values, x ~ U[-1,1) (seed 3) -- a synthetic stand-in for the
 paper's Spin-26 matrix.  One step = one b = A x through the library's
 SymmSpMV path (schedule built before timing, as the paper excludes
-preprocessing).  The full-CRS SpMV of the same permuted matrix is timed
-beside it as the traffic baseline.
+preprocessing).  Beside it, on the same permuted matrix: the full-CRS SpMV
+(the traffic baseline), the all-FP64 executor (the plain FP64 form), the
+conflict-free RACE executors, the input order, FP32-stored values, and the
+reductions alone.  The default run also measures the other workloads of the
+paper's classes, each in its own block of the line: the 27-point stencil
+200^3 (SymmSpMV, FP32-stored values with their error against the FP64
+oracle, SymmSpMM k = 4, 8, 16 in FP64 and FP32 values), the Anderson model
+32^3 (L2-resident: time only), and the batch of 64 matrices in one CUDA
+graph.
+
+Roofline: algorithmic bytes (v+4) nnz_u + 4 N + 24 k N (x read, b read and
+written: the count of Eq. "SymmSpMV_intensity" at the optimal alpha, which
+the reduction-based executors also move: b is zeroed, accumulated in L2 and
+written back) over the launch's CUDA-event time, against the measured copy
+bandwidth and, as the paper's range, the load-only bandwidth measured here;
+SymmSpMM also against min(HBM * I, FP64 FMA rate measured here).
 
 Timing: W warm-up steps, then K steps bracketed by a barrier and
 torch.cuda.synchronize(), CUDA events on the stream the kernels run on;
@@ -16,8 +30,10 @@ matrix is 1.05 GB, so every step's inputs exceed the 129 MB L2.  Several
 GPUs (torchrun) run independent replicas (no data exchange); value is the
 sum over ranks of the flops divided by the slowest rank's time.
 
---impl reference times the CPU oracle (serial FP64 Alg. "SymmSpMV") on a
-bounded number of sweeps of the same matrix on the host cores.
+--impl reference times the oracle's CPU RACE execution (the paper's own
+method: the oracle's schedule for N_t = host threads, phases in order with a
+barrier, the leaves of a phase on the host cores) on bounded repetitions of
+the same matrix.
 """
 from __future__ import annotations
 
@@ -43,16 +59,11 @@ WORKLOAD_DESC = {
     "batch64": "64 matrices: Anderson L~U[16,96] and geometric graphs n~U[1e4,1e6] (mean degree 20), FP64, k=4",
 }
 
-
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
-
-
-# SymmSpMM right-hand-side counts timed per workload (the 27-point stencil: k = 4, 8, 16)
-SPMM_KS = {"st27_200": (4, 8, 16), "st27_100": (16,)}
 
 
 def max_over_ranks(times, world, device):
@@ -198,17 +209,24 @@ def oracle_cpu(m, name, seconds):
     }
 
 
-def oracle_normwise_error(m, x, b_perm, perm):
+def oracle_normwise_error(m, x, b_perm, perm, ref=None):
     """||b - b_ref||_2 / || |A||x| ||_2 of a result b (given in the schedule's
     permuted order) against the FP64 oracle's plain definition (part of the
-    CPU-baseline leg: the only place bench.py runs the oracle)."""
+    CPU-baseline leg: the only place bench.py runs the oracle).  `ref` may
+    carry the oracle's (b_ref, |A||x|) from an earlier call on the same m, x."""
     import numpy as np
 
     import oracle
-    bref, s = oracle.spmv_full(oracle.expand_full(m), x)
+    bref, s = ref if ref is not None else oracle.spmv_full(oracle.expand_full(m), x)
     b = np.empty_like(bref)
     b[perm] = b_perm
     return float(np.linalg.norm(b - bref) / np.linalg.norm(s))
+
+
+def oracle_reference(m, x):
+    """The oracle's (b_ref, |A||x|) for oracle_normwise_error."""
+    import oracle
+    return oracle.spmv_full(oracle.expand_full(m), x)
 
 
 # the metric of both arms (the reference arm times the oracle's RACE
@@ -236,6 +254,103 @@ def run_reference(args):
     return 0
 
 
+
+
+class Timer:
+    """CUDA-event timing on one stream: warm-up, barrier + synchronize on both
+    sides of the timed region (the rule of every timed number here)."""
+
+    def __init__(self, stream, dev, world):
+        self.stream, self.dev, self.world = stream, dev, world
+
+    def barrier(self):
+        if self.world > 1:
+            import torch
+            torch.distributed.barrier()
+
+    def __call__(self, fn, steps, warmup):
+        import torch
+        for i in range(warmup):
+            fn(i)
+        self.stream.synchronize()
+        self.barrier()
+        torch.cuda.synchronize(self.dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for i in range(steps):
+            fn(i)
+        e1.record(self.stream)
+        torch.cuda.synchronize(self.dev)
+        self.barrier()
+        return e0.elapsed_time(e1) * 1e-3
+
+
+def measure_ceilings(R, dev, stream, timer):
+    """The load-only HBM bandwidth (2 GiB streamed once per call, best of 5)
+    and the FP64 fused multiply-add rate, both with race_probe_peaks."""
+    import torch
+    n = 1 << 28
+    with torch.cuda.stream(stream):
+        buf = torch.ones(n, dtype=torch.float64, device=dev)
+        out = torch.empty(4096, dtype=torch.float64, device=dev)
+    best = min(timer(lambda i: R.race_probe_peaks(0, buf, n, out, 1, stream), 1, 1) for _ in range(5))
+    load_gbs = 8.0 * n / best / 1e9
+    del buf
+    iters = 4096
+    threads = torch.cuda.get_device_properties(dev).multi_processor_count * 4 * 256
+    t = min(timer(lambda i: R.race_probe_peaks(1, None, 0, out, iters, stream), 1, 1) for _ in range(3))
+    dfma = 8.0 * iters * threads / t
+    torch.cuda.empty_cache()
+    return {"load_only_gbs": load_gbs, "fp64_fma_per_s": dfma,
+            "how": "race_probe_peaks: 2 GiB read once with 16-byte streaming loads (best of 5); eight "
+                   "independent FP64 FMA chains per thread, 1024 threads per SM (best of 3)"}
+
+
+def roofline_block(nbytes, seconds, peak, peak_kind, load_gbs, traffic=None, overwrite_bytes=None):
+    """HBM roofline of one launch: algorithmic bytes over its time against
+    the measured copy peak (and the load-only bandwidth, the paper's range)."""
+    achieved = nbytes / seconds / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_step": nbytes,
+           "load_only_peak": load_gbs, "frac_of_load_only": achieved / load_gbs if load_gbs else None}
+    if overwrite_bytes is not None:
+        out["algorithmic_bytes_overwrite"] = overwrite_bytes
+        out["frac_overwrite_count"] = overwrite_bytes / seconds / 1e9 / peak
+    return out
+
+
+def spmm_roof(flops, nbytes, seconds, hbm_gbs, dfma_per_s):
+    """SymmSpMM against min(HBM * I, FP64 roof): I = flops / bytes; the FP64
+    roof is 2 flops per fused multiply-add at the measured rate."""
+    intensity = flops / nbytes
+    roof = min(hbm_gbs * 1e9 * intensity, 2.0 * dfma_per_s)
+    achieved = flops / seconds
+    return {"intensity_flop_per_byte": intensity, "roof_gflops": roof / 1e9,
+            "bound": "hbm" if hbm_gbs * 1e9 * intensity < 2.0 * dfma_per_s else "fp64",
+            "frac_of_roof": achieved / roof, "frac_hbm": nbytes / seconds / 1e9 / hbm_gbs}
+
+
+# SymmSpMM right-hand-side counts timed in the 27-point stencil block
+SPMM_KS = (4, 8, 16)
+RING = 4  # x and b buffers rotated over the timed steps
+
+
+def arithmetic_label(launch):
+    """What the launch computes in: FP64, or FP64 row sums with a share of
+    double-float transposed products (the products' relative error is below
+    2^-44 each; x, b and the accumulation stay FP64)."""
+    ex = launch.get("executor")
+    if ex in (8, 9):
+        q = launch.get("fp64_quarters", 0)
+        return (f"f64 row sums; transposed products f64 in {q}/4 of the warps and double-float "
+                f"(Dekker products of FP32 halves, joined to f64 before the reduction) in {4 - q}/4")
+    if ex == 10:
+        return (f"row sums f64 in {launch.get('rowsum_fp64_quarters', 4)}/4 of the warps (rest double-float), "
+                f"transposed products f64 in {launch.get('fp64_quarters', 0)}/4 (rest double-float)")
+    return "f64"
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -254,6 +369,10 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     R.lib()
+    stream = torch.cuda.Stream(device=dev)
+    timed = Timer(stream, dev, world)
+    peak, peak_kind = load_peaks()
+    ceil = measure_ceilings(R, dev, stream, timed)
 
     name = args.workload
     m = configs.matrix(name)
@@ -261,9 +380,8 @@ def run_ours(args):
     n, nu = m["n"], len(m["col"])
     nf = 2 * nu - n
     t0 = time.perf_counter()
-    stream = torch.cuda.Stream(device=dev)
     s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
-                     rcm=cfg.get("rcm", False))
+                     rcm=cfg.get("rcm", False), windows=False)
     build_s = time.perf_counter() - t0
     lc = cfg["launch"]
     R.race_set_launch(s, 0, **lc)
@@ -274,55 +392,39 @@ def run_ours(args):
     perm = s.perm()
     x_host = configs.vectors(name, n)
 
-    ring = 4
     with torch.cuda.stream(stream):
         xs = []
-        for i in range(ring):
+        for i in range(RING):
             xo = torch.from_numpy(x_host).to(dev) if i == 0 else torch.rand(n, dtype=torch.float64, device=dev)
             xp = torch.empty_like(xo)
             R.race_permute(s, xo, xp, 1, stream)
             xs.append(xp)
-        bs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(ring)]
+        bs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(RING)]
     stream.synchronize()
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def timed(fn, steps, warmup):
-        for i in range(warmup):
-            fn(i)
-        stream.synchronize()
-        barrier()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(steps):
-            fn(i)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-        return e0.elapsed_time(e1) * 1e-3
 
     # ---- main timed region: SymmSpMV -------------------------------------------------------
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    t_symm = timed(lambda i: R.symm_spmv(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    t_symm = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     clk = clocks.stop()
     R.race_poll_status(s, stream)
+    # ---- the plain FP64 form: the all-FP64 row-parallel executor on the same schedule --------
+    R.race_set_launch(s, 0, executor=R.RACE_EXEC_ROWS_RED, group_lanes=1, rows_per_group=1, blocks_per_sm=0,
+                      regs_per_row=8, fp64_quarters=4)
+    t_strict = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
+    R.race_set_launch(s, 0, **lc)
     # ---- the limit the reduction-based executors share: the scatter's reductions at L2 ------
     def probe(mode):
         def step(i):
             if mode == 0:
-                bs[i % ring].zero_()
-            R.race_probe_scatter(s, mode, bs[i % ring], stream)
+                bs[i % RING].zero_()
+            R.race_probe_scatter(s, mode, bs[i % RING], stream)
         with torch.cuda.stream(stream):
             return timed(step, args.steps, args.warmup)
     t_red, t_col = probe(0), probe(1)
     # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
-    t_full = timed(lambda i: R.spmv_full(s, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    t_full = timed(lambda i: R.spmv_full(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     # ---- the conflict-free RACE executors (a few steps: they are slow) on the schedule that
     # suits them (full recursion), one row per thread in the leaf executor
     cf = cfg["conflict_free"]
@@ -330,8 +432,8 @@ def run_ours(args):
                         one_level_stage0=cf.get("one_level_stage0", False))
     info_cf = s_cf.info()
     R.race_set_launch(s_cf, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
-    t_leaf_cta = timed(lambda i: R.symm_spmv(s_cf, xs[i % ring], bs[i % ring], stream), 3, 1)
-    t_win_race = timed(lambda i: R.symm_spmv_exec(s_cf, R.RACE_EXEC_WINDOW_RACE, xs[i % ring], bs[i % ring],
+    t_leaf_cta = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), 3, 1)
+    t_win_race = timed(lambda i: R.symm_spmv_exec(s_cf, R.RACE_EXEC_WINDOW_RACE, xs[i % RING], bs[i % RING],
                                                   stream), 3, 1)
     s_cf.free()
     # ---- the same two kernels on the input order (no RACE permutation) --------------------
@@ -339,35 +441,18 @@ def run_ours(args):
     R.race_set_launch(s_nat, 0, **lc)
     R.race_prepare_full(s_nat, stream)
     R.race_set_launch(s_nat, 1, **fl)
-    t_nat_symm = timed(lambda i: R.symm_spmv(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
-    t_nat_full = timed(lambda i: R.spmv_full(s_nat, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
+    t_nat_symm = timed(lambda i: R.symm_spmv(s_nat, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
+    t_nat_full = timed(lambda i: R.spmv_full(s_nat, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     s_nat.free()
-    # ---- FP32-stored values (x, b and the row sums stay FP64), same launch -----------------
-    s32 = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
-                       val_type=R.RACE_F32, windows=False, rcm=cfg.get("rcm", False))
+    # ---- FP32-stored values (x, b and the row sums stay FP64), same schedule and launch ----
+    s32 = R.race_import(m, s.export(), stream=stream, val_type=R.RACE_F32, windows=False)
     R.race_set_launch(s32, 0, **lc)
-    t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % ring], bs[i % ring], stream), args.steps, args.warmup)
-    # the FP32-valued result for x_host, kept for the normwise error against the FP64 oracle
+    t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     with torch.cuda.stream(stream):
         R.symm_spmv(s32, xs[0], bs[0], stream)
     stream.synchronize()
     b32_perm = bs[0].cpu().numpy()
     s32.free()
-    # ---- SymmSpMM with several right-hand sides (workloads that name them) ------------------
-    spmm = {}
-    for k in SPMM_KS.get(name, ()):
-        with torch.cuda.stream(stream):
-            Xk = [torch.rand(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
-            Bk = [torch.empty(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
-        # the project's autotuner picks this k's launch shape, then the timed steps run it
-        tuned, _ = R.race_autotune(s, k, Xk[0], Bk[0], reps=3, stream=stream)
-        tk = timed(lambda i: R.symm_spmm(s, k, Xk[i % 2], Bk[i % 2], stream), max(3, args.steps // 4), 2)
-        per_k = tk / max(3, args.steps // 4)
-        spmm[str(k)] = {"ms_per_step": per_k * 1e3, "gflops": pm.flops(nf, k) / per_k / 1e9,
-                        "gbs": pm.symm_bytes(n, nu, k) / per_k / 1e9, "launch": tuned}
-        del Xk, Bk
-    if spmm:
-        R.race_set_launch(s, 0, **lc)  # the SymmSpMV launch again
     # ---- end to end through host buffers: H2D x, permute, SymmSpMV, unpermute, D2H b --------
     # Each step copies its x in and its b out; copies run on their own streams
     # (double-buffered), so step i's read-back overlaps step i+1's upload and
@@ -401,7 +486,7 @@ def run_ours(args):
         for i in range(warmup):
             e2e_step(i)
         torch.cuda.synchronize(dev)
-        barrier()
+        timed.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -411,7 +496,7 @@ def run_ours(args):
         stream.wait_stream(s_out)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        barrier()
+        timed.barrier()
         return e0.elapsed_time(e1) * 1e-3
 
     t_e2e = timed_e2e(args.steps, args.warmup)
@@ -423,55 +508,69 @@ def run_ours(args):
     ref = bd[0].cpu().numpy()
     got = bh[(args.steps - 1) % 2].numpy()
     e2e_ok = bool(np.allclose(got, ref, rtol=1e-12, atol=1e-12 * float(np.abs(ref).max())))
-    t_symm, t_full, t_e2e, t_red, t_col = max_over_ranks([t_symm, t_full, t_e2e, t_red, t_col], world, dev)
+    t_symm, t_full, t_e2e, t_red, t_col, t_strict = max_over_ranks([t_symm, t_full, t_e2e, t_red, t_col, t_strict],
+                                                                   world, dev)
+    s.free()
+    del xs, bs, xd, bd, xpd, bpd
+    torch.cuda.empty_cache()
 
     flops = pm.flops(nf)
     per_step = t_symm / args.steps
     value = whole_job_rate(world, flops, args.steps, t_symm) / 1e9
     full_gflops = whole_job_rate(world, flops, args.steps, t_full) / 1e9
     e2e_value = whole_job_rate(world, flops, args.steps, t_e2e) / 1e9
-    sym_bytes = pm.symm_bytes(n, nu)
-    achieved = sym_bytes / per_step / 1e9
-    peak, peak_kind = load_peaks()
     launches_per_step = 1 if lc["executor"] >= R.RACE_EXEC_ATOMIC else info["n_phases"]
+
+    # ---- the other workloads of the default run (rank 0's replica measures them too) --------
+    extra = {}
+    if not args.no_extra and name == "xxz26":
+        extra["st27_200"] = stencil_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, ceil, local)
+        extra["anderson32"] = small_block(args, R, configs, pm, dev, stream, timed)
+        extra["batch64"] = batch_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, e2e=False)
     if rank != 0:
         return 0
 
-    # CPU baseline: the oracle on a bounded sample (a few serial sweeps)
+    # CPU baseline: the oracle on a bounded sample, and the FP32-value error against it
     cpu = None
     fp32_err = None
     if not args.no_cpu_baseline:
         cpu = oracle_cpu(m, name, args.cpu_seconds)
         fp32_err = oracle_normwise_error(m, x_host, b32_perm, perm)
     traffic = ncu_traffic(name, "symm")
+    sym_bytes = pm.symm_bytes_rmw(n, nu)
     line = {
         "metric": METRIC_SYMM,
         "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64+df64" if lc["executor"] in (8, 9, 10) else "f64", "arithmetic": arithmetic_label(lc),
+        "data": "synthetic",
         "config": {"workload": name, "desc": WORKLOAD_DESC.get(name, name), "n": n, "nnz_upper": nu, "nnz_full": nf,
                    "l2": "inputs larger than L2 (matrix 1.05 GB; x, b rotate over 4+4 buffers of 83 MB)",
                    "schedule": {"n_workers": cfg["n_workers"], "eps": list(cfg["eps"]), "n_phases": info["n_phases"],
                                 "eta": info["eta"], "depth": info["depth"], "rcm": bool(cfg.get("rcm", False))},
                    "launch": lc, "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_step": sym_bytes},
-        "symm_gbs": achieved,
+        "roofline": roofline_block(sym_bytes, per_step, peak, peak_kind, ceil["load_only_gbs"], traffic,
+                                   pm.symm_bytes(n, nu)),
+        "ceilings": ceil,
+        "strict_fp64": {"ms_per_step": t_strict / args.steps * 1e3,
+                        "gflops": flops / (t_strict / args.steps) / 1e9,
+                        "frac": sym_bytes / (t_strict / args.steps) / 1e9 / peak,
+                        "launch": "RACE_EXEC_ROWS_RED, one row per lane, all arithmetic FP64 (the plain FP64 form)"},
         "reduction_floor": {"ms_per_step": t_red / args.steps * 1e3, "columns_only_ms_per_step": t_col / args.steps * 1e3,
                             "frac": (t_red / args.steps) / per_step,
                             "what": "race_probe_scatter on the same schedule: the transposed update's L2 reductions "
                                     "alone (mode 0, b zeroed first) and its column stream alone (mode 1), with the "
                                     "executors' access pattern; frac = that floor / SymmSpMV time"},
         "spmv_full": {"value": full_gflops, "unit": "GFLOP/s", "ms_per_step": t_full / args.steps * 1e3,
-                      "gbs": pm.full_bytes(n, nf) / (t_full / args.steps) / 1e9},
+                      "gbs": pm.full_bytes(n, nf) / (t_full / args.steps) / 1e9,
+                      "frac": pm.full_bytes(n, nf) / (t_full / args.steps) / 1e9 / peak},
         "fp32_values": {"ms_per_step": t_f32 / args.steps * 1e3, "gflops": flops / (t_f32 / args.steps) / 1e9,
-                        "gbs": pm.symm_bytes(n, nu, 1, 4) / (t_f32 / args.steps) / 1e9,
+                        "gbs": pm.symm_bytes_rmw(n, nu, 1, 4) / (t_f32 / args.steps) / 1e9,
                         "normwise_error_vs_fp64_oracle": fp32_err,
                         "what": "values stored in FP32 (8 B per stored entry), x, b and row sums FP64; error = "
                                 "||b32 - b_ref||_2 / || |A||x| ||_2 against the FP64 oracle (computed in the CPU "
-                                "baseline leg; null without it)"},
-        "spmm": spmm,
+                                "baseline leg; null without it).  The XXZ values (+-1/2, multiples of 1/4) are "
+                                "exact in FP32: the 27-point stencil block carries the error that matters"},
         "natural_order": {"symm_ms_per_step": t_nat_symm / args.steps * 1e3,
                           "symm_gflops": flops / (t_nat_symm / args.steps) / 1e9,
                           "full_ms_per_step": t_nat_full / args.steps * 1e3,
@@ -496,17 +595,278 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "build_seconds": build_s,
     }
+    line.update(extra)
     print(json.dumps(line))
-    s.free()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_batch(args):
+def stencil_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, ceil, local):
+    """The 27-point stencil 200^3 (paper: HPCG-like matrices): SymmSpMV in the
+    benchmark's launch and in plain FP64, FP32-stored values with their
+    normwise error against the FP64 oracle, the full-CRS SpMV, and SymmSpMM
+    k = 4, 8, 16 (FP64 and FP32 values, each width autotuned first) against
+    min(HBM * I, FP64 roof)."""
+    import torch
+
+    name = "st27_200"
+    m = configs.matrix(name)
+    cfg = configs.SCHEDULE[name]
+    n, nu = m["n"], len(m["col"])
+    nf = 2 * nu - n
+    t0 = time.perf_counter()
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream,
+                     rcm=cfg.get("rcm", False), windows=False)
+    s32 = R.race_import(m, s.export(), stream=stream, val_type=R.RACE_F32, windows=False)
+    build_s = time.perf_counter() - t0
+    lc = cfg["launch"]
+    R.race_set_launch(s, 0, **lc)
+    R.race_set_launch(s32, 0, **lc)
+    R.race_prepare_full(s, stream)
+    R.race_set_launch(s, 1, **cfg["full_launch"])
+    info = s.info()
+    perm = s.perm()
+    x_host = configs.vectors(name, n)
+    with torch.cuda.stream(stream):
+        xs = [torch.from_numpy(x_host[perm].copy()).to(dev)] + \
+             [torch.rand(n, dtype=torch.float64, device=dev) for _ in range(RING - 1)]
+        bs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(RING)]
+    stream.synchronize()
+    K, W = args.steps, args.warmup
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t_symm = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), K, W) / K
+    clk = clocks.stop()
+    with torch.cuda.stream(stream):
+        R.symm_spmv(s, xs[0], bs[0], stream)
+    stream.synchronize()
+    b64_perm = bs[0].cpu().numpy()
+    R.race_set_launch(s, 0, executor=R.RACE_EXEC_ROWS_RED, group_lanes=1, rows_per_group=1, blocks_per_sm=0,
+                      regs_per_row=8, fp64_quarters=4)
+    t_strict = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), K, W) / K
+    R.race_set_launch(s, 0, **lc)
+    t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % RING], bs[i % RING], stream), K, W) / K
+    with torch.cuda.stream(stream):
+        R.symm_spmv(s32, xs[0], bs[0], stream)
+    stream.synchronize()
+    b32_perm = bs[0].cpu().numpy()
+    t_full = timed(lambda i: R.spmv_full(s, xs[i % RING], bs[i % RING], stream), K, W) / K
+    del xs, bs
+    torch.cuda.empty_cache()
+    flops = pm.flops(nf)
+    hbm = peak
+    out = {
+        "workload": name, "desc": WORKLOAD_DESC[name], "n": n, "nnz_upper": nu, "nnz_full": nf,
+        "schedule": {"n_workers": cfg["n_workers"], "max_depth": cfg["max_depth"], "rcm": bool(cfg.get("rcm")),
+                     "n_phases": info["n_phases"], "eta": info["eta"]},
+        "launch": lc, "arithmetic": arithmetic_label(lc), "build_seconds": build_s, "clocks": clk,
+        "symm_spmv": {"ms_per_step": t_symm * 1e3, "gflops": flops / t_symm / 1e9,
+                      "roofline": roofline_block(pm.symm_bytes_rmw(n, nu), t_symm, hbm, peak_kind,
+                                                 ceil["load_only_gbs"], None, pm.symm_bytes(n, nu))},
+        "strict_fp64": {"ms_per_step": t_strict * 1e3, "gflops": flops / t_strict / 1e9,
+                        "frac": pm.symm_bytes_rmw(n, nu) / t_strict / 1e9 / hbm},
+        "fp32_values": {"ms_per_step": t_f32 * 1e3, "gflops": flops / t_f32 / 1e9,
+                        "frac": pm.symm_bytes_rmw(n, nu, 1, 4) / t_f32 / 1e9 / hbm},
+        "spmv_full": {"ms_per_step": t_full * 1e3, "gflops": flops / t_full / 1e9,
+                      "frac": pm.full_bytes(n, nf) / t_full / 1e9 / hbm},
+        "speedup_vs_full": t_full / t_symm,
+        "l2": "inputs larger than L2 (matrix 1.33 GB; x, b rotate over 4+4 buffers of 64 MB)",
+    }
+    if not args.no_cpu_baseline:
+        ref = oracle_reference(m, x_host)
+        out["fp32_values"]["normwise_error_vs_fp64_oracle"] = oracle_normwise_error(m, x_host, b32_perm, perm, ref)
+        out["symm_spmv"]["normwise_error_vs_fp64_oracle"] = oracle_normwise_error(m, x_host, b64_perm, perm, ref)
+        del ref
+    # SymmSpMM: each width and value type tuned by the project's autotuner, then timed
+    spmm = {}
+    steps = max(3, K // 4)
+    for k in SPMM_KS:
+        with torch.cuda.stream(stream):
+            Xk = [torch.rand(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+            Bk = [torch.empty(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+        for vt, sk, vb in (("f64", s, 8), ("f32", s32, 4)):
+            tuned, _ = R.race_autotune(sk, k, Xk[0], Bk[0], reps=3, stream=stream)
+            tk = timed(lambda i: R.symm_spmm(sk, k, Xk[i % 2], Bk[i % 2], stream), steps, 2) / steps
+            fk, bk = pm.flops(nf, k), pm.symm_bytes_rmw(n, nu, k, vb)
+            spmm[f"k{k}_{vt}"] = {"ms_per_step": tk * 1e3, "gflops": fk / tk / 1e9, "gbs": bk / tk / 1e9,
+                                  "launch": tuned, "arithmetic": arithmetic_label(tuned),
+                                  **spmm_roof(fk, bk, tk, hbm, ceil["fp64_fma_per_s"])}
+        del Xk, Bk
+        torch.cuda.empty_cache()
+    out["spmm"] = spmm
+    s.free()
+    s32.free()
+    torch.cuda.empty_cache()
+    return out
+
+
+def small_block(args, R, configs, pm, dev, stream, timed):
+    """The Anderson model 32^3 (2.5 MB: L2-resident, no HBM-roof claim):
+    every call timed alone with its own events, L2 flushed (a 256 MB write)
+    between calls; the benchmark's executor, the full-CRS SpMV and the
+    paper's execution model (leaf per block, phases in order)."""
+    import torch
+
+    name = "anderson32"
+    m = configs.matrix(name)
+    cfg = configs.SCHEDULE[name]
+    n, nu = m["n"], len(m["col"])
+    nf = 2 * nu - n
+    s = R.race_build(m, cfg["n_workers"], eps=cfg["eps"], max_depth=cfg["max_depth"], stream=stream, windows=False)
+    R.race_set_launch(s, 0, **cfg["launch"])
+    R.race_prepare_full(s, stream)
+    R.race_set_launch(s, 1, **cfg["full_launch"])
+    info = s.info()
+    with torch.cuda.stream(stream):
+        x = torch.from_numpy(configs.vectors(name, n)[s.perm()].copy()).to(dev)
+        b = torch.empty_like(x)
+        flush = torch.empty(1 << 25, dtype=torch.float64, device=dev)
+
+    def per_call(fn, calls):
+        ts = []
+        for i in range(calls + 3):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts)
+
+    calls = max(10, args.steps)
+    t_symm = per_call(lambda: R.symm_spmv(s, x, b, stream), calls)
+    t_full = per_call(lambda: R.spmv_full(s, x, b, stream), calls)
+    t_leaf = per_call(lambda: R.symm_spmv_exec(s, R.RACE_EXEC_LEAF_CTA, x, b, stream), calls)
+    s.free()
+    del flush
+    torch.cuda.empty_cache()
+    flops = pm.flops(nf)
+    return {"workload": name, "desc": WORKLOAD_DESC[name], "n": n, "nnz_upper": nu,
+            "launch": cfg["launch"], "schedule": {"n_workers": cfg["n_workers"], "n_phases": info["n_phases"],
+                                                  "eta": info["eta"]},
+            "symm_us": t_symm * 1e6, "symm_gflops": flops / t_symm / 1e9, "spmv_full_us": t_full * 1e6,
+            "leaf_cta_us": t_leaf * 1e6, "speedup_vs_full": t_full / t_symm,
+            "timing": "median of per-call CUDA-event times, L2 flushed by a 256 MB write before each call",
+            "roofline": "none claimed: 2.5 MB of matrix, L2- and latency-bound (as the paper treats its "
+                        "L2-resident matrices)"}
+
+
+def batch_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, e2e=True):
     """64 matrices (Anderson L in [16,96] and geometric graphs n in [1e4,1e6]),
-    SymmSpMM with k = 4, each schedule autotuned, all replayed by one CUDA graph."""
+    SymmSpMM with k = 4, each schedule built on a host thread and autotuned,
+    all replayed by one CUDA graph.  With e2e: every X up and every B down per
+    step as well (two buffer sets and graphs alternating)."""
+    import concurrent.futures as cf
     import numpy as np
+    import torch
+
+    k = 4
+    t0 = time.perf_counter()
+    mats = configs.batch64()
+    bsch = configs.BATCH_SCHEDULE
+
+    def build(m):
+        return R.race_build(m, bsch["n_workers"], max_depth=bsch["max_depth"], rcm=bsch.get("rcm", False),
+                            host_only=True, windows=False)
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        scheds = list(ex.map(build, mats))
+    scheds_built = time.perf_counter() - t0
+    Xs, Bs, Xh = [], [], []
+    flops = 0
+    sym_bytes = 0
+    tuned = {}
+    for i, (m, s) in enumerate(zip(mats, scheds)):
+        R.race_upload(s, stream)
+        n, nu = m["n"], len(m["col"])
+        X = configs.matgen.uniform(n * k, 300 + i).reshape(n, k)
+        xp = torch.from_numpy(np.ascontiguousarray(X[s.perm()])).to(dev)
+        bp = torch.empty_like(xp)
+        launch, _ = R.race_autotune(s, k, xp, bp, reps=3, stream=stream)
+        key = f"{launch['executor']}/{launch['rows_per_group']}/{launch['blocks_per_sm']}"
+        tuned[key] = tuned.get(key, 0) + 1
+        Xs.append(xp)
+        Bs.append(bp)
+        Xh.append(X)
+        flops += pm.flops(2 * nu - n, k)
+        sym_bytes += pm.symm_bytes_rmw(n, nu, k)
+    batch = R.race_batch_create(scheds, k, Xs, Bs, stream)
+    setup_s = time.perf_counter() - t0
+    stream.synchronize()
+    t = timed(lambda i: batch.launch(stream), args.steps, args.warmup)
+    per = t / args.steps
+    out = {"workload": "batch64", "desc": WORKLOAD_DESC["batch64"], "k": k, "matrices": len(mats),
+           "rows": int(sum(m["n"] for m in mats)), "schedule": dict(bsch), "tuned_launches": tuned,
+           "ms_per_step": per * 1e3, "gflops": flops / per / 1e9, "flops_per_step": flops,
+           "roofline": roofline_block(sym_bytes, per, peak, peak_kind, None),
+           "setup_seconds": setup_s, "schedule_build_seconds": scheds_built,
+           "l2": "inputs larger than L2 (all matrices and blocks: several GB per replay)",
+           "note": "most matrices are small (L2- and latency-bound): the HBM fraction is not the measure here"}
+    if e2e:
+        xh = [torch.from_numpy(np.ascontiguousarray(X[s.perm()])).pin_memory() for X, s in zip(Xh, scheds)]
+        bh = [[torch.empty_like(h).pin_memory() for h in xh] for _ in range(2)]
+        X2 = [Xs, [torch.empty_like(x) for x in Xs]]
+        B2 = [Bs, [torch.empty_like(b) for b in Bs]]
+        batches = [batch, R.race_batch_create(scheds, k, X2[1], B2[1], stream)]
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+
+        def e2e_step(i):
+            j = i % 2
+            s_in.wait_event(ev_c[j])
+            with torch.cuda.stream(s_in):
+                for h, d in zip(xh, X2[j]):
+                    d.copy_(h, non_blocking=True)
+            ev_in[j].record(s_in)
+            stream.wait_event(ev_in[j])
+            stream.wait_event(ev_out[j])
+            batches[j].launch(stream)
+            ev_c[j].record(stream)
+            s_out.wait_event(ev_c[j])
+            with torch.cuda.stream(s_out):
+                for h, d in zip(bh[j], B2[j]):
+                    h.copy_(d, non_blocking=True)
+            ev_out[j].record(s_out)
+
+        for i in range(args.warmup):
+            e2e_step(i)
+        torch.cuda.synchronize(dev)
+        timed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        for i in range(args.steps):
+            e2e_step(i)
+        stream.wait_stream(s_out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        timed.barrier()
+        t_e2e = e0.elapsed_time(e1) * 1e-3
+        last = (args.steps - 1) % 2
+        ok = all(bool(np.allclose(h.numpy(), d.cpu().numpy(), rtol=1e-12, atol=1e-300))
+                 for h, d in zip(bh[last], B2[last]))
+        batches[1].free()
+        nbytes = sum(x.numel() * 8 for x in xh)
+        out["e2e"] = {"seconds": t_e2e, "steps": args.steps, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes, "ms_per_step": t_e2e / args.steps * 1e3,
+                      "matches_device_result": ok,
+                      "how": "per step: pinned H2D of every X, one graph replay, D2H of every B; two buffer sets "
+                             "and graphs alternate, copies on their own streams"}
+    batch.free()
+    for s in scheds:
+        s.free()
+    del Xs, Bs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    """The batch workload on its own line (the metric of that config)."""
     import torch
 
     import paper_1907_06487_gb300 as R
@@ -521,131 +881,33 @@ def run_batch(args):
         B.build()
     if world > 1:
         torch.distributed.barrier()
-    k = 4
-    mats = configs.batch64()
     stream = torch.cuda.Stream(device=dev)
-    t0 = time.perf_counter()
-    scheds, Xs, Bs, Xh = [], [], [], []
-    flops = 0
-    sym_bytes = 0
-    tuned = {}
-    for i, m in enumerate(mats):
-        s = R.race_build(m, configs.BATCH_SCHEDULE["n_workers"], max_depth=configs.BATCH_SCHEDULE["max_depth"],
-                         stream=stream, rcm=configs.BATCH_SCHEDULE.get("rcm", False))
-        n, nu = m["n"], len(m["col"])
-        X = configs.matgen.uniform(n * k, 300 + i).reshape(n, k)
-        xp = torch.from_numpy(np.ascontiguousarray(X[s.perm()])).to(dev)
-        bp = torch.empty_like(xp)
-        launch, _ = R.race_autotune(s, k, xp, bp, reps=3, stream=stream)
-        key = f"{launch['executor']}/{launch['rows_per_group']}/{launch['blocks_per_sm']}"
-        tuned[key] = tuned.get(key, 0) + 1
-        scheds.append(s); Xs.append(xp); Bs.append(bp); Xh.append(X)
-        flops += pm.flops(2 * nu - n, k)
-        sym_bytes += pm.symm_bytes(n, nu, k)
-    batch = R.race_batch_create(scheds, k, Xs, Bs, stream)
-    setup_s = time.perf_counter() - t0
-    stream.synchronize()
-
-    def timed(fn, steps, warmup):
-        for i in range(warmup):
-            fn(i)
-        stream.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(steps):
-            fn(i)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-        return e0.elapsed_time(e1) * 1e-3
-
+    timed = Timer(stream, dev, world)
+    peak, peak_kind = load_peaks()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
-    t = timed(lambda i: batch.launch(stream), args.steps, args.warmup)
+    blk = batch_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, e2e=True)
     clk = clocks.stop()
-    # end to end: H2D of every X from pinned host memory, graph, D2H of every B.  Two buffer
-    # sets with a graph each, alternating, copies on their own streams: step i's read-back
-    # overlaps step i+1's upload and replay.
-    xh = [torch.from_numpy(np.ascontiguousarray(X[s.perm()])).pin_memory() for X, s in zip(Xh, scheds)]
-    bh = [[torch.empty_like(h).pin_memory() for h in xh] for _ in range(2)]
-    X2 = [Xs, [torch.empty_like(x) for x in Xs]]
-    B2 = [Bs, [torch.empty_like(b) for b in Bs]]
-    batches = [batch, R.race_batch_create(scheds, k, X2[1], B2[1], stream)]
-    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
-
-    def e2e(i):
-        j = i % 2
-        s_in.wait_event(ev_c[j])
-        with torch.cuda.stream(s_in):
-            for h, d in zip(xh, X2[j]):
-                d.copy_(h, non_blocking=True)
-        ev_in[j].record(s_in)
-        stream.wait_event(ev_in[j])
-        stream.wait_event(ev_out[j])
-        batches[j].launch(stream)
-        ev_c[j].record(stream)
-        s_out.wait_event(ev_c[j])
-        with torch.cuda.stream(s_out):
-            for h, d in zip(bh[j], B2[j]):
-                h.copy_(d, non_blocking=True)
-        ev_out[j].record(s_out)
-
-    def timed_e2e(steps, warmup):
-        for i in range(warmup):
-            e2e(i)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s_in.wait_stream(stream)
-        for i in range(steps):
-            e2e(i)
-        stream.wait_stream(s_out)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-        return e0.elapsed_time(e1) * 1e-3
-
-    t_e2e = timed_e2e(args.steps, args.warmup)
-    # the read-back of the last step equals the graph's result on the same X
-    last = (args.steps - 1) % 2
-    e2e_ok = all(bool(np.allclose(h.numpy(), d.cpu().numpy(), rtol=1e-12, atol=1e-300))
-                 for h, d in zip(bh[last], B2[last]))
-    batches[1].free()
-    t, t_e2e = max_over_ranks([t, t_e2e], world, dev)
-    per = t / args.steps
-    achieved = sym_bytes / per / 1e9
-    peak, peak_kind = load_peaks()
+    t, t_e2e = max_over_ranks([blk["ms_per_step"] * 1e-3 * args.steps, blk["e2e"]["seconds"]], world, dev)
     if rank == 0:
-        nbytes = sum(x.numel() * 8 for x in xh)
+        flops = blk["flops_per_step"]
+        e2e = dict(blk.pop("e2e"))
+        e2e_line = {"value": whole_job_rate(world, flops, args.steps, t_e2e) / 1e9, "unit": "GFLOP/s",
+                    **{k: e2e[k] for k in ("h2d_bytes_per_step", "d2h_bytes_per_step", "ms_per_step",
+                                           "matches_device_result", "how")}}
         print(json.dumps({
             "metric": "SymmSpMM GFLOP/s (2*nnz_full*k flops) of a 64-matrix batch in one CUDA graph",
-            "value": whole_job_rate(world, flops, args.steps, t) / 1e9, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch64", "k": k, "matrices": len(mats),
-                       "rows": int(sum(m["n"] for m in mats)), "schedule": dict(configs.BATCH_SCHEDULE),
-                       "tuned_launches": tuned,
-                       "l2": "inputs larger than L2 (all matrices and blocks: several GB per replay)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_step": sym_bytes},
-            "e2e": {"value": whole_job_rate(world, flops, args.steps, t_e2e) / 1e9, "unit": "GFLOP/s",
-                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                    "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
-                    "how": "per step: pinned H2D of every X, one graph replay, D2H of every B; two buffer sets "
-                           "and graphs alternate, copies on their own streams"},
-            "gpu_launches": len(mats) * args.steps, "clocks": clk, "cpu_baseline": None,
-            "setup_seconds": setup_s}))
-    batch.free()
+            "value": whole_job_rate(world, flops, args.steps, t) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+df64",
+            "data": "synthetic", "config": {"workload": "batch64", **{k: blk[k] for k in
+                                                                      ("k", "matrices", "rows", "schedule",
+                                                                       "tuned_launches", "l2")}},
+            "roofline": blk["roofline"], "e2e": e2e_line, "gpu_launches": None, "clocks": clk,
+            "cpu_baseline": None, "setup_seconds": blk["setup_seconds"],
+            "note": "gpu_launches: one CUDA graph replay per step holding the 64 matrices' kernels"}))
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -657,6 +919,8 @@ def build_parser():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="xxz26", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="measure the headline workload only (no stencil, Anderson and batch blocks)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     return ap

@@ -311,6 +311,21 @@ int race_get_launch(const race_schedule *s, int32_t which, race_launch *l);
  * doubles.  RACE_ERR_INVALID for another mode.                            */
 int race_probe_scatter(const race_schedule *s, int32_t mode, double *b_d, void *stream);
 
+/* race_probe_peaks — diagnostic ceilings for the roofline, computes nothing
+ * of SymmSpMV.  The paper's roofline takes its memory term as a range from
+ * the load-only to the copy bandwidth (Sec. 3, Table "test bed"); GB300's
+ * FP64 rate is the second roof of the FP64-heavy SymmSpMM.
+ *   what = 0: reads in_d[0, n) once (16-byte loads, streaming), the bits
+ *             of each block's words folded by XOR into out_d[block]: time it
+ *             for the load-only bandwidth (8 n bytes);
+ *   what = 1: eight independent chains of `iters` FP64 fused multiply-adds
+ *             per thread: 8 * iters * threads FMAs, threads = 1024 per SM.
+ * Grid: 4 blocks of 256 threads per SM; out_d: device array of at least
+ * 4096 doubles.  in_d (what 0): device, 16-byte aligned.
+ * Errors: RACE_ERR_INVALID (bad what, n < 0, misaligned input, iters < 1),
+ * _UNSUPPORTED (more than 4096 blocks), _CUDA.                            */
+int race_probe_peaks(int32_t what, const double *in_d, int64_t n, double *out_d, int32_t iters, void *stream);
+
 /* race_poll_status — synchronises `stream`, then returns RACE_ERR_TIMEOUT
  * (and clears it) if a bounded device wait of this schedule's kernels gave
  * up since the last poll, else RACE_OK.                                    */

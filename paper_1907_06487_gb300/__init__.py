@@ -50,7 +50,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
             "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz",
-            "race_probe_wait_timeout")
+            "race_probe_wait_timeout", "race_probe_peaks")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -143,6 +143,8 @@ def lib():
     L.race_probe_scatter.restype = ctypes.c_int
     L.race_poll_status.argtypes = [vp, vp]
     L.race_poll_status.restype = ctypes.c_int
+    L.race_probe_peaks.argtypes = [i32, vp, ctypes.c_int64, vp, i32, vp]
+    L.race_probe_peaks.restype = ctypes.c_int
     L.race_probe_wait_timeout.argtypes = [vp, vp, vp, vp]
     L.race_probe_wait_timeout.restype = ctypes.c_int
     L.symm_spmv_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, vp, vp, vp, vp]
@@ -361,6 +363,13 @@ def race_probe_scatter(s: Schedule, mode, b, stream=None):
 
 def race_poll_status(s: Schedule, stream=None):
     _check(lib().race_poll_status(s.handle, _stream(stream)), "race_poll_status")
+
+
+def race_probe_peaks(what, inp, n, out, iters=1, stream=None):
+    """Diagnostic ceilings: what 0 streams n doubles of inp (load-only
+    bandwidth), what 1 runs FP64 fused multiply-add chains (iters each)."""
+    _check(lib().race_probe_peaks(int(what), _ptr(inp), int(n), _ptr(out), int(iters), _stream(stream)),
+           "race_probe_peaks")
 
 
 def race_probe_wait_timeout(s: Schedule, x, b, stream=None):

@@ -40,7 +40,10 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # measured N_t sweep that builds in seconds), with stage-0 groups of one
 # level (upper storage keeps them write-disjoint; 27-point 100^3: 99 -> 63
 # phases, leaf-per-CTA executor 0.996 -> 0.741 ms).
-_L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=5, regs_per_row=4, fp64_quarters=2)
+# (XXZ L=26 sweep of blocks per SM x entries per step x FP64 share: 6 blocks of
+# 40-register threads, 4 entries, half the warps' transposed products in FP64
+# lead, 0.322 ms against 0.328 at 5 blocks and 0.330-0.345 at shares 1 and 0)
+_L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=6, regs_per_row=4, fp64_quarters=2)
 _LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=8, fp64_quarters=2)
 _F = dict(executor=2, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=16)
 SCHEDULE = {

@@ -10,6 +10,8 @@ The optimal alpha is 1/N_nzr (SpMV) and 1/N_nzr^symm (SymmSpMV).
 GPU algorithmic bytes (no write-allocate; b overwritten, so b is written
 once and never has to be read): with v the bytes of a stored value,
   SymmSpMV, k RHS:  (v + 4) nnz_u + 4 (N + 1) + 8 k N (X read) + 8 k N (B written)
+  with B read as well (zeroed, accumulated, written back: the paper's count
+  at alpha_opt):    (v + 4) nnz_u + 4 N + 24 k N
   full SpMV, k RHS: (v + 4) nnz_f + 4 (N + 1) + 8 k N + 8 k N
 Both count every byte the operation must move at least once; flops are
 2 nnz_f k for both, so GF/s of the two kernels compare directly.
@@ -45,6 +47,14 @@ def perf(intensity: float, bandwidth: float) -> float:
 def symm_bytes(n: int, nnz_u: int, k: int = 1, val_bytes: int = 8) -> int:
     """Minimum bytes of B = A X from upper CRS on a GPU (see module doc)."""
     return (val_bytes + 4) * nnz_u + 4 * (n + 1) + 16 * k * n
+
+
+def symm_bytes_rmw(n: int, nnz_u: int, k: int = 1, val_bytes: int = 8) -> int:
+    """Bytes of B = A X from upper CRS when B is read and written once besides
+    X read once: the count of Eq. SymmSpMV_intensity at the optimal alpha
+    (24 bytes of vector traffic per row and right-hand side).  The executors
+    that zero B and accumulate the transposed update at L2 move this much."""
+    return (val_bytes + 4) * nnz_u + 4 * n + 24 * k * n
 
 
 def full_bytes(n: int, nnz_f: int, k: int = 1, val_bytes: int = 8) -> int:

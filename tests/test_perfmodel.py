@@ -46,3 +46,15 @@ def test_gpu_traffic_figures():
     assert pm.full_bytes(n, nf) == 12 * nf + 4 * (n + 1) + 16 * n
     assert pm.flops(nf) == 302033424
     assert pm.symm_bytes(n, nu, val_bytes=4) == pm.symm_bytes(n, nu) - 4 * nu
+
+
+def test_accumulate_byte_count_is_the_papers_intensity_at_optimal_alpha():
+    """symm_bytes_rmw equals the bytes of Eq. SymmSpMV_intensity at
+    alpha = 1 / N_nzr^symm (4 flops per stored nonzero over the intensity),
+    on the XXZ L=26 and 27-point 200^3 sizes."""
+    for n, nu in ((10400600, 80708656), (8000000, 110923596)):
+        nsym = nu / n
+        nnzr = 2.0 * (nsym - 1.0) + 1.0  # inverse of Eq. NNZR_symm
+        paper = nu * 4.0 / pm.i_symm_spmv(1.0 / nsym, nnzr)
+        assert pm.symm_bytes_rmw(n, nu) == pytest.approx(paper, rel=1e-12)
+        assert pm.symm_bytes_rmw(n, nu) - pm.symm_bytes(n, nu) == 8 * n - 4
