@@ -60,6 +60,9 @@ def _get():
     L.orc_expand_full.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i64p, _i32p, _f64p]
     L.orc_spmv_full.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, _f64p, _f64p, _f64p]
     L.orc_spmm_full.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, ctypes.c_int32, _f64p, _f64p, _f64p]
+    L.orc_matrix_powers.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, ctypes.c_int32, _f64p, _f64p, _f64p,
+                                    _f64p]
+    L.orc_matrix_powers.restype = None
     L.orc_symm_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
     L.orc_symm_spmv_race.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p, _i32p,
                                      _f64p, _f64p, ctypes.c_int32]
@@ -145,6 +148,17 @@ def spmm_full(full, X):
     _get().orc_spmm_full(n, _p(full["row_ptr"], _i64p), _p(full["col"], _i32p), _p(full["val"], _f64p),
                          k, _p(X, _f64p), _p(B, _f64p), _p(S, _f64p))
     return B, S
+
+
+def matrix_powers(full, x, p):
+    """Y[:, q] = A^(q+1) x and S[:, q] = |A|^(q+1) |x| (n x p arrays) on a full
+    CRS from ``expand_full``: the definition applied p times (R13)."""
+    n = full["n"]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    Y = np.zeros((p, n)); S = np.zeros((p, n)); tmp = np.zeros(n)
+    _get().orc_matrix_powers(n, _p(full["row_ptr"], _i64p), _p(full["col"], _i32p), _p(full["val"], _f64p),
+                             int(p), _p(x, _f64p), _p(Y, _f64p), _p(S, _f64p), _p(tmp, _f64p))
+    return Y.T.copy(), S.T.copy()
 
 
 def symm_spmv(m, x):

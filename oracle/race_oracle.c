@@ -24,6 +24,8 @@
  *                      over CPU threads (OpenMP), no s
  *   orc_symm_gs        symmetric Gauss-Seidel sweeps under a schedule (R11)
  *   orc_symm_kacz      symmetric Kaczmarz sweeps under a schedule (R12)
+ *   orc_matrix_powers  Y[:, q] = A^(q+1) x for q < p, the definition applied
+ *                      p times, with |A|^(q+1) |x| for the bound (R13)
  *
  * Schedule part (integer + FP64 control arithmetic), Section 4:
  *   level construction (Alg. "Construction of levels", Eq. "level"),
@@ -81,6 +83,11 @@
  *      matrix in the schedule's order.
  *   R12 symmetric Kaczmarz on a schedule: the same passes, each row
  *      projecting x onto its hyperplane (writes every column of the row).
+ *   R13 matrix powers: the paper names in-place matrix powers as future work
+ *      only.  Read as the powers A x, A^2 x, ..., A^p x written as the p
+ *      columns of one n x p array, each computed from the previous column
+ *      (no vector storage besides the output); the values are those of the
+ *      plain definition, whatever the order of evaluation.
  */
 #ifdef _OPENMP
 #include <omp.h>
@@ -139,6 +146,24 @@ void orc_spmv_full(int32_t n, const int64_t *frp, const int32_t *fci, const doub
         }
         b[row] = tmp;
         if (s) s[row] = a;
+    }
+}
+
+/* Matrix powers (R13: the paper's conclusion names in-place matrix powers
+ * among the kernels a level-based formulation serves).  Y is n x p, column
+ * q (entries q*n .. q*n+n-1) = A^(q+1) x: the plain definition applied p
+ * times, each power to the previous one (Alg. "SpMV using the CRS format" on
+ * the full matrix).  S (NULL to skip), same shape, = |A|^(q+1) |x|: every
+ * rounding of power q is bounded in terms of it.  tmp: n doubles of
+ * scratch when S is given.                                                */
+void orc_matrix_powers(int32_t n, const int64_t *frp, const int32_t *fci, const double *fva, int32_t p,
+                       const double *x, double *Y, double *S, double *tmp) {
+    for (int32_t q = 0; q < p; ++q) {
+        const double *src = q == 0 ? x : Y + (int64_t)(q - 1) * n;
+        orc_spmv_full(n, frp, fci, fva, src, Y + (int64_t)q * n, q == 0 && S ? S : NULL);
+        if (S && q > 0) /* |A| S_{q-1}: S_{q-1} >= 0, so the s output of the
+                           definition applied to it is exactly that        */
+            orc_spmv_full(n, frp, fci, fva, S + (int64_t)(q - 1) * n, tmp, S + (int64_t)q * n);
     }
 }
 
