@@ -423,6 +423,8 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             return timed(step, args.steps, args.warmup)
     t_red, t_col = probe(0), probe(1)
+    mpk = mpk_block(R, pm, s, n, nu, dev, stream, timed, args.steps, peak)
+    R.race_set_launch(s, 0, **lc)
     # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
     t_full = timed(lambda i: R.spmv_full(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     # ---- the conflict-free RACE executors (a few steps: they are slow) on the schedule that
@@ -586,6 +588,7 @@ def run_ours(args):
                                        "leaves share an entry of b; x and b in that schedule's order) on a fully "
                                        "recursed schedule, 3 steps each"},
         "speedup_vs_full": t_full / t_symm,
+        "matrix_powers": mpk,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
                 "how": "per step: pinned H2D of x, permute, SymmSpMV, unpermute, D2H of b into pinned memory; "
@@ -653,12 +656,14 @@ def stencil_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, cei
     stream.synchronize()
     b32_perm = bs[0].cpu().numpy()
     t_full = timed(lambda i: R.spmv_full(s, xs[i % RING], bs[i % RING], stream), K, W) / K
+    mpk = mpk_block(R, pm, s, n, nu, dev, stream, timed, K, peak)
     del xs, bs
     torch.cuda.empty_cache()
     flops = pm.flops(nf)
     hbm = peak
     out = {
         "workload": name, "desc": WORKLOAD_DESC[name], "n": n, "nnz_upper": nu, "nnz_full": nf,
+        "matrix_powers": mpk,
         "schedule": {"n_workers": cfg["n_workers"], "max_depth": cfg["max_depth"], "rcm": bool(cfg.get("rcm")),
                      "n_phases": info["n_phases"], "eta": info["eta"]},
         "launch": lc, "arithmetic": arithmetic_label(lc), "build_seconds": build_s, "clocks": clk,
@@ -698,6 +703,60 @@ def stencil_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, cei
     out["spmm"] = spmm
     s.free()
     s32.free()
+    torch.cuda.empty_cache()
+    out["gauss_seidel_kaczmarz"] = sweeps_block(args, R, configs, pm, dev, stream, timed, peak)
+    return out
+
+
+def mpk_block(R, pm, s, n, nu, dev, stream, timed, steps, peak, p=4):
+    """Matrix powers A x .. A^p x on a schedule (its SymmSpMV launch): p
+    sweeps against the level wavefront, bytes p times a SymmSpMV's."""
+    import torch
+    with torch.cuda.stream(stream):
+        x = torch.rand(n, dtype=torch.float64, device=dev)
+        Y = torch.empty(p * n, dtype=torch.float64, device=dev)
+    out = {"p": p}
+    k = max(3, steps // 4)
+    for label, mode in (("sweeps", R.RACE_MPK_SWEEPS), ("wavefront", R.RACE_MPK_WAVEFRONT)):
+        R.race_matrix_powers(s, p, x, Y, mode, stream)  # first use builds the wavefront's block table
+        t = timed(lambda i: R.race_matrix_powers(s, p, x, Y, mode, stream), k, 2) / k
+        out[label] = {"ms_per_call": t * 1e3, "ms_per_power": t / p * 1e3,
+                      "frac": p * pm.symm_bytes_rmw(n, nu) / t / 1e9 / peak}
+    R.race_poll_status(s, stream)
+    del x, Y
+    return out
+
+
+def sweeps_block(args, R, configs, pm, dev, stream, timed, peak):
+    """Symmetric Gauss-Seidel and symmetric Kaczmarz sweeps on the 27-point
+    stencil under the fully recursed schedule the leaf executors use (the
+    paper's execution model: phases in order, one leaf per lane group)."""
+    import torch
+    name = "st27_200"
+    m = configs.matrix(name)
+    cfg = configs.SCHEDULE[name]
+    cf = cfg["sweeps"]
+    n, nu = m["n"], len(m["col"])
+    nf = 2 * nu - n
+    t0 = time.perf_counter()
+    s = R.race_build(m, cf["n_workers"], eps=cfg["eps"], max_depth=cf["max_depth"], stream=stream,
+                     rcm=cfg.get("rcm", False), windows=False)
+    R.race_prepare_full(s, stream)
+    build_s = time.perf_counter() - t0
+    info = s.info()
+    with torch.cuda.stream(stream):
+        b = torch.rand(n, dtype=torch.float64, device=dev)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+    out = {"schedule": {"n_workers": cf["n_workers"], "max_depth": cf["max_depth"], "n_phases": info["n_phases"],
+                        "n_leaves": info["n_leaves"], "eta": info["eta"]}, "build_seconds": build_s}
+    sweeps = 3
+    for label, fn in (("symm_gs", R.symm_gs), ("symm_kacz", R.symm_kacz)):
+        fn(s, b, x, 1, stream)
+        t = timed(lambda i: fn(s, b, x, sweeps, stream), 1, 1) / sweeps
+        out[label] = {"ms_per_sweep": t * 1e3, "gbs": pm.sweep_bytes(n, nf) / t / 1e9,
+                      "frac": pm.sweep_bytes(n, nf) / t / 1e9 / peak}
+    s.free()
+    del b, x
     torch.cuda.empty_cache()
     return out
 

@@ -386,6 +386,30 @@ int symm_gs(const race_schedule *s, const double *b_d, double *x_d, int32_t swee
  * errors as for symm_gs; a zero row gives inf or nan entries.              */
 int symm_kacz(const race_schedule *s, const double *b_d, double *x_d, int32_t sweeps, void *stream);
 
+/* race_matrix_powers — the powers A x, A^2 x, ..., A^p x of the symmetric
+ * matrix (the paper's conclusion names in-place matrix powers among the
+ * kernels a level-based formulation serves): column q of Y (entries
+ * q*n .. q*n+n-1) = A^(q+1) x, each column computed from the previous one,
+ * no vector storage besides Y.  x_d: n doubles, Y_d: n*p doubles, device,
+ * permuted order, not overlapping; Y is overwritten.  1 <= p <= 64.
+ *   RACE_MPK_SWEEPS: p calls of symm_spmv with the schedule's executor.
+ *   RACE_MPK_WAVEFRONT: one cooperative launch over (power, row block)
+ *     items: block t of power q starts once power q-1 is complete up to the
+ *     last block that block t's columns reach (in level order the rows of a
+ *     level couple only to the neighbouring levels, Sec. 4.1), so several
+ *     powers advance together over the matrix.  Arithmetic as
+ *     RACE_EXEC_DF64_RED with the schedule's fp64_quarters (all FP64 when a
+ *     stored value lies outside the double-float range).  FP64-stored values
+ *     only.  The first call builds the block table on the host and uploads
+ *     it (allocates and waits for `stream`), and a call with a larger p than
+ *     before allocates its done flags: make those calls outside stream
+ *     capture.  Every wait is bounded; race_poll_status reports a timeout.
+ * Errors: RACE_ERR_INVALID (NULL, overlap, p, mode), _UNSUPPORTED (host-only
+ * schedule; FP32 values in the wavefront mode), _NOMEM, _CUDA.            */
+#define RACE_MPK_SWEEPS 0
+#define RACE_MPK_WAVEFRONT 1
+int race_matrix_powers(race_schedule *s, int32_t p, const double *x_d, double *Y_d, int32_t mode, void *stream);
+
 /* Build and upload the full CRS used by spmv_full now (optional).          */
 int race_prepare_full(race_schedule *s, void *stream);
 

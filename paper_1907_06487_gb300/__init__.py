@@ -50,7 +50,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
             "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz",
-            "race_probe_wait_timeout", "race_probe_peaks")
+            "race_probe_wait_timeout", "race_probe_peaks", "race_matrix_powers")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -144,6 +144,8 @@ def lib():
     L.race_poll_status.argtypes = [vp, vp]
     L.race_poll_status.restype = ctypes.c_int
     L.race_probe_peaks.argtypes = [i32, vp, ctypes.c_int64, vp, i32, vp]
+    L.race_matrix_powers.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.race_matrix_powers.restype = ctypes.c_int
     L.race_probe_peaks.restype = ctypes.c_int
     L.race_probe_wait_timeout.argtypes = [vp, vp, vp, vp]
     L.race_probe_wait_timeout.restype = ctypes.c_int
@@ -330,6 +332,16 @@ def race_import(m, image: bytes, host_only=False, stream=None, val_type=RACE_F64
 
 def symm_spmv(s: Schedule, x, b, stream=None):
     _check(lib().symm_spmv(s.handle, _ptr(x), _ptr(b), _stream(stream)), "symm_spmv")
+
+
+RACE_MPK_SWEEPS = 0
+RACE_MPK_WAVEFRONT = 1
+
+
+def race_matrix_powers(s: Schedule, p, x, Y, mode=RACE_MPK_WAVEFRONT, stream=None):
+    """Y[:, q] = A^(q+1) x (Y: n*p doubles, column q at q*n), permuted order."""
+    _check(lib().race_matrix_powers(s.handle, int(p), _ptr(x), _ptr(Y), int(mode), _stream(stream)),
+           "race_matrix_powers")
 
 
 def symm_gs(s: Schedule, b, x, sweeps=1, stream=None):

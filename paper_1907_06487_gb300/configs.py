@@ -39,7 +39,9 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # `conflict_free` is the schedule they are measured on (the fastest of the
 # measured N_t sweep that builds in seconds), with stage-0 groups of one
 # level (upper storage keeps them write-disjoint; 27-point 100^3: 99 -> 63
-# phases, leaf-per-CTA executor 0.996 -> 0.741 ms).
+# phases, leaf-per-CTA executor 0.996 -> 0.741 ms).  `sweeps` is the schedule
+# of the Gauss-Seidel and Kaczmarz sweeps (distance-2 phases throughout: the
+# Kaczmarz update writes every column of a row).
 # (XXZ L=26 sweep of blocks per SM x entries per step x FP64 share: 6 blocks of
 # 40-register threads, 4 entries, half the warps' transposed products in FP64
 # lead, 0.322 ms against 0.328 at 5 blocks and 0.330-0.345 at shares 1 and 0)
@@ -53,7 +55,8 @@ SCHEDULE = {
     "xxz24": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, executor=1, launch=_L, full_launch=_F,
                   conflict_free=dict(n_workers=152, max_depth=-1, one_level_stage0=True)),
     "st27_200": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, rcm=True, executor=1, launch=_LP,
-                     full_launch=_F, conflict_free=dict(n_workers=2432, max_depth=-1, one_level_stage0=True)),
+                     full_launch=_F, conflict_free=dict(n_workers=2432, max_depth=-1, one_level_stage0=True),
+                     sweeps=dict(n_workers=2432, max_depth=-1)),
     "st27_100": dict(n_workers=152, eps=(0.8, 0.8, 0.5), max_depth=1, rcm=True, executor=1, launch=_LP,
                      full_launch=_F, conflict_free=dict(n_workers=2432, max_depth=-1, one_level_stage0=True)),
 }

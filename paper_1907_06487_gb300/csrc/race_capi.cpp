@@ -28,9 +28,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void release_device(race_schedule* s) {
     void* ptrs[] = {s->d_rp, s->d_col, s->d_val, s->d_leaf_lo, s->d_leaf_hi, s->d_perm,
-                    s->d_frp, s->d_fcol, s->d_fval, s->d_blk, s->d_fblk, s->d_status};
+                    s->d_frp, s->d_fcol, s->d_fval, s->d_blk, s->d_fblk, s->d_status,
+                    s->mpk.d_reach, s->mpk.d_flags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    s->mpk = MpkState();
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;

@@ -108,6 +108,16 @@ struct SellSet {
     bool ready = false;
 };
 
+// Level-wavefront matrix powers (mpk_kernels.cu): row blocks of `rows`
+// rows; reach[t] = the last block that rows of block t touch; `lag` = max_t
+// (reach[t] - t); the flags (a ticket counter, then one done flag per power
+// and block) are allocated on first use for up to `flag_powers` powers.
+struct MpkState {
+    int32_t rows = 0, nblk = 0, lag = 0, flag_powers = 0;
+    int32_t* d_reach = nullptr;
+    int32_t* d_flags = nullptr;
+};
+
 // The opaque handle of the C ABI.
 struct race_schedule {
     race::Plan plan;
@@ -149,6 +159,7 @@ struct race_schedule {
     // symm_kacz: phases checked on first use for distance-2 independence on
     // the full rows (0 = not checked, 1 = independent, -1 = not)
     mutable std::atomic<int32_t> kacz_state{0};
+    MpkState mpk;  // matrix powers, level wavefront (built on first use)
 };
 
 // Row blocks for the streaming kernels: consecutive rows with at most

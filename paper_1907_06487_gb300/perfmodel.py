@@ -62,6 +62,13 @@ def full_bytes(n: int, nnz_f: int, k: int = 1, val_bytes: int = 8) -> int:
     return (val_bytes + 4) * nnz_f + 4 * (n + 1) + 16 * k * n
 
 
+def sweep_bytes(n: int, nnz_f: int, val_bytes: int = 8) -> int:
+    """Bytes of one symmetric Gauss-Seidel or Kaczmarz sweep on the full CRS:
+    a forward and a backward pass, each reading the matrix, b, and x and
+    writing x once."""
+    return 2 * ((val_bytes + 4) * nnz_f + 4 * (n + 1) + 24 * n)
+
+
 def flops(nnz_f: int, k: int = 1) -> int:
     """Useful flops of B = A X (one multiply and one add per full nonzero and column)."""
     return 2 * nnz_f * k
