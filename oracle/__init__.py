@@ -63,6 +63,9 @@ def _get():
     L.orc_matrix_powers.argtypes = [ctypes.c_int32, _i64p, _i32p, _f64p, ctypes.c_int32, _f64p, _f64p, _f64p,
                                     _f64p]
     L.orc_matrix_powers.restype = None
+    L.orc_coloring.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p,
+                               _i32p, _i32p]
+    L.orc_coloring.restype = ctypes.c_int32
     L.orc_symm_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
     L.orc_symm_spmv_race.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p, _i32p,
                                      _f64p, _f64p, ctypes.c_int32]
@@ -148,6 +151,22 @@ def spmm_full(full, X):
     _get().orc_spmm_full(n, _p(full["row_ptr"], _i64p), _p(full["col"], _i32p), _p(full["val"], _f64p),
                          k, _p(X, _f64p), _p(B, _f64p), _p(S, _f64p))
     return B, S
+
+
+def coloring(m, method, block_rows=1):
+    """MC (method 0) or ABMC (method 1, blocks of block_rows rows) schedule of
+    an upper-CRS matrix dict: (perm, stage_ptr, leaf_lo, leaf_hi) (R14)."""
+    n, rp, ci, va = _mat(m)
+    bs = 1 if method == 0 else int(block_rows)
+    units = (n + bs - 1) // bs
+    perm = np.zeros(max(n, 1), np.int32)
+    sp = np.zeros(units + 2, np.int32)
+    lo = np.zeros(max(units, 1), np.int32)
+    hi = np.zeros(max(units, 1), np.int32)
+    nl = np.zeros(1, np.int32)
+    ncol = _get().orc_coloring(n, _p(rp, _i32p), _p(ci, _i32p), int(method), bs, _p(perm, _i32p), _p(sp, _i32p),
+                               _p(lo, _i32p), _p(hi, _i32p), _p(nl, _i32p))
+    return perm[:n], sp[:ncol + 1], lo[:nl[0]], hi[:nl[0]]
 
 
 def matrix_powers(full, x, p):

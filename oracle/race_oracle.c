@@ -24,6 +24,7 @@
  *                      over CPU threads (OpenMP), no s
  *   orc_symm_gs        symmetric Gauss-Seidel sweeps under a schedule (R11)
  *   orc_symm_kacz      symmetric Kaczmarz sweeps under a schedule (R12)
+ *   orc_coloring       MC / ABMC multicolouring schedules (R14)
  *   orc_matrix_powers  Y[:, q] = A^(q+1) x for q < p, the definition applied
  *                      p times, with |A|^(q+1) |x| for the bound (R13)
  *
@@ -83,6 +84,9 @@
  *      matrix in the schedule's order.
  *   R12 symmetric Kaczmarz on a schedule: the same passes, each row
  *      projecting x onto its hyperplane (writes every column of the row).
+ *   R14 multicolouring schedules (MC, ABMC): the paper compares with COLPACK
+ *      and METIS; written here from its description, first-fit colouring in
+ *      unit order, ABMC blocks = consecutive rows of the given order.
  *   R13 matrix powers: the paper names in-place matrix powers as future work
  *      only.  Read as the powers A x, A^2 x, ..., A^p x written as the p
  *      columns of one n x p array, each computed from the previous column
@@ -1002,6 +1006,72 @@ void orc_symm_kacz(int32_t n, const int64_t *frp, const int32_t *fci, const doub
                     }
             }
     }
+}
+
+/* Multicolouring schedules (R14: the paper's comparison methods, Sec. 3.3
+ * and 6.3).  Units: rows (method 0, MC) or blocks of block_rows consecutive
+ * rows (method 1, ABMC).  A unit takes the smallest colour not held by an
+ * earlier unit that has a row within graph distance 2 of one of its rows
+ * (distance in the symmetric graph, self-loops ignored).  Output: perm
+ * (units colour by colour, units and their rows in order), stage_ptr (one
+ * phase per colour, n_colours + 1 offsets into the leaves), leaf_lo/hi (one
+ * leaf per unit, positions in the permuted order).  Returns the number of
+ * colours; *n_leaves gets the number of units.                            */
+int32_t orc_coloring(int32_t n, const int32_t *rp, const int32_t *ci, int32_t method, int32_t block_rows,
+                     int32_t *perm, int32_t *stage_ptr, int32_t *leaf_lo, int32_t *leaf_hi, int32_t *n_leaves) {
+    const int32_t bs = method == 0 ? 1 : block_rows;
+    const int32_t units = (n + bs - 1) / bs;
+    int64_t *aptr = calloc((size_t)n + 1, sizeof(int64_t));
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = rp[r]; t < rp[r + 1]; ++t)
+            if (ci[t] != r) { aptr[r + 1]++; aptr[ci[t] + 1]++; }
+    for (int32_t r = 0; r < n; ++r) aptr[r + 1] += aptr[r];
+    int32_t *adj = malloc(sizeof(int32_t) * (size_t)(aptr[n] > 0 ? aptr[n] : 1));
+    int64_t *pos = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t r = 0; r < n; ++r) pos[r] = aptr[r];
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t t = rp[r]; t < rp[r + 1]; ++t)
+            if (ci[t] != r) { adj[pos[r]++] = ci[t]; adj[pos[ci[t]]++] = r; }
+    int32_t *color = malloc(sizeof(int32_t) * (size_t)(units > 0 ? units : 1));
+    /* used[c] != 0: colour c is held by an earlier unit near the current one */
+    uint8_t *used = calloc((size_t)units + 1, 1);
+    int32_t *seen = malloc(sizeof(int32_t) * (size_t)(units + 1));
+    int32_t nseen, ncol = 0;
+    for (int32_t u = 0; u < units; ++u) {
+        nseen = 0;
+        int32_t r1 = (u + 1) * bs < n ? (u + 1) * bs : n;
+        for (int32_t r = u * bs; r < r1; ++r) {
+            /* rows within distance 0, 1 and 2 of r */
+            for (int64_t a = aptr[r] - 1; a < aptr[r + 1]; ++a) {
+                int32_t w = a < aptr[r] ? r : adj[a];
+                for (int64_t b = aptr[w] - 1; b < aptr[w + 1]; ++b) {
+                    int32_t v = b < aptr[w] ? w : adj[b];
+                    int32_t vu = v / bs;
+                    if (vu < u && !used[color[vu]]) { used[color[vu]] = 1; seen[nseen++] = color[vu]; }
+                }
+            }
+        }
+        int32_t c = 0;
+        while (used[c]) ++c;
+        color[u] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+        for (int32_t k = 0; k < nseen; ++k) used[seen[k]] = 0;
+    }
+    int32_t q = 0, row = 0;
+    for (int32_t c = 0; c < ncol; ++c) {
+        stage_ptr[c] = q;
+        for (int32_t u = 0; u < units; ++u) {
+            if (color[u] != c) continue;
+            int32_t r1 = (u + 1) * bs < n ? (u + 1) * bs : n;
+            leaf_lo[q] = row;
+            for (int32_t r = u * bs; r < r1; ++r) perm[row++] = r;
+            leaf_hi[q++] = row;
+        }
+    }
+    stage_ptr[ncol] = q;
+    *n_leaves = q;
+    free(aptr); free(adj); free(pos); free(color); free(used); free(seen);
+    return ncol;
 }
 
 /* The pseudo-peripheral vertex reached from `start` on the symmetric graph
