@@ -13,8 +13,17 @@ plain stores, one launch per phase), and the fastest point is the label.
 The exhaustive sweep stays both the fallback and the judge of the
 predictor's regret.
 
-Usage (GPU):  python -m paper_1907_06487_gb300.predictor sweep   (writes data/predictor_sweep.npz)
-              python -m paper_1907_06487_gb300.predictor train   (writes data/predictor.f32)
+A second data set (dataset_matrix_v2, config sizes: stencils of side 16..128,
+XXZ L = 16..24, geometric and band matrices of 10^4..10^6 rows) is swept over
+GRID_V2 with the executors that run all rows at once (the library's default)
+and one leaf per block, N_t = 152; a network is trained per executor.  Every
+evaluation reports the paper's default point and the best single fixed grid
+point chosen on the training matrices beside the network.
+
+Usage (GPU):  python -m paper_1907_06487_gb300.predictor sweep        (data/predictor_sweep.npz)
+              python -m paper_1907_06487_gb300.predictor train        (data/predictor.f32)
+              python -m paper_1907_06487_gb300.predictor sweep_full   (data/predictor_sweep_full.npz)
+              python -m paper_1907_06487_gb300.predictor train_full   (data/predictor_full_*.f32)
 """
 from __future__ import annotations
 
@@ -27,9 +36,36 @@ import numpy as np
 from . import RACE_EXEC_LEAF_GROUP, lib, matgen, race_build, race_features, symm_spmv_exec
 from . import race_mlp_adam, race_mlp_backward, race_mlp_forward
 
-GRID_EPS = (0.5, 0.6, 0.7, 0.8, 0.9)
-GRID_DEPTH = (1, 2, 3, 4, -1)
-GRID = [(e0, e1, d) for e0 in GRID_EPS for e1 in GRID_EPS for d in GRID_DEPTH]
+class Grid:
+    """A grid of schedule parameters (eps_0, eps_1, depth), eps_s = 0.5 for
+    s > 1; depth -1 = as deep as the epsilon rule goes (the paper)."""
+
+    def __init__(self, eps, depth):
+        self.eps, self.depth = tuple(eps), tuple(depth)
+        self.points = [(e0, e1, d) for e0 in self.eps for e1 in self.eps for d in self.depth]
+
+    def __len__(self):
+        return len(self.points)
+
+    def index(self, e0, e1, d):
+        return self.points.index((e0, e1, d))
+
+    def encode(self, e0, e1, d):
+        """Target in [0,1]^3 for a grid point."""
+        ne, nd = len(self.eps) - 1, len(self.depth) - 1
+        return np.array([self.eps.index(e0) / ne, self.eps.index(e1) / ne, self.depth.index(d) / nd], np.float32)
+
+    def decode(self, y):
+        """Nearest grid point of a network output."""
+        y = np.clip(np.asarray(y, dtype=np.float64), 0.0, 1.0)
+        ne, nd = len(self.eps) - 1, len(self.depth) - 1
+        return (self.eps[int(np.rint(y[0] * ne))], self.eps[int(np.rint(y[1] * ne))],
+                self.depth[int(np.rint(y[2] * nd))])
+
+
+# the scaled-down data set, labelled with the schedule-bound executor
+GRID_V1 = Grid((0.5, 0.6, 0.7, 0.8, 0.9), (1, 2, 3, 4, -1))
+GRID_EPS, GRID_DEPTH, GRID = GRID_V1.eps, GRID_V1.depth, GRID_V1.points
 PAPER_POINT = (0.8, 0.8, -1)
 SWEEP_WORKERS = 128
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -37,21 +73,15 @@ DATA = os.path.join(HERE, "data")
 
 
 def point_index(e0, e1, d):
-    return GRID.index((e0, e1, d))
+    return GRID_V1.index(e0, e1, d)
 
 
 def encode(e0, e1, d):
-    """Target in [0,1]^3 for a grid point."""
-    return np.array([(e0 - 0.5) / 0.4, (e1 - 0.5) / 0.4, GRID_DEPTH.index(d) / 4.0], np.float32)
+    return GRID_V1.encode(e0, e1, d)
 
 
 def decode(y):
-    """Nearest grid point of a network output."""
-    y = np.clip(np.asarray(y, dtype=np.float64), 0.0, 1.0)
-    e0 = GRID_EPS[int(np.rint(y[0] * 4))]
-    e1 = GRID_EPS[int(np.rint(y[1] * 4))]
-    d = GRID_DEPTH[int(np.rint(y[2] * 4))]
-    return e0, e1, d
+    return GRID_V1.decode(y)
 
 
 def dataset_matrix(i, count=500, seed=9):
@@ -80,6 +110,38 @@ def dataset_matrix(i, count=500, seed=9):
 
 def dataset_matrices(count=500, seed=9):
     return [dataset_matrix(i, count, seed) for i in range(count)]
+
+
+# the data set at the sizes of the paper-shaped families, labelled with the
+# executors that run all rows at once (the library's default) and one leaf per
+# block (the conflict-free one), N_t = 152 as in the benchmark's schedules
+GRID_V2 = Grid((0.5, 0.65, 0.8, 0.9), (1, 2, 3, -1))
+SWEEP_WORKERS_V2 = 152
+V2_LAUNCH = {"default": dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4,
+                             fp64_quarters=2),
+             "leafcta": dict(executor=1, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=8)}
+
+
+def dataset_matrix_v2(i, count=500, seed=10):
+    """Matrix i of the full-size data set: 7-pt and 27-pt stencils of side
+    16..128, XXZ chains L = 16..24 (even), random geometric graphs and random
+    band matrices (bandwidth 50..500) of 10^4..10^6 rows, mean degree 20;
+    sizes log-uniform."""
+    u = matgen.uniform(3 * count, seed, 0.0, 1.0)
+    a, b = u[3 * i], u[3 * i + 1]
+    kind = i % 4
+    if kind == 0:
+        side = int(round(16 * 8.0 ** a))
+        npt = 7 if b < 0.5 else 27
+        return f"stencil{npt}_{side}", matgen.stencil3d(side, npt=npt, seed=1000 + i)
+    if kind == 1:
+        L = 16 + 2 * min(4, int(a * 5))
+        return f"xxz{L}", matgen.xxz(L)
+    n = int(10.0 ** (4.0 + 2.0 * a))
+    if kind == 2:
+        return f"geometric{n}", matgen.geometric(n, seed=2000 + i)
+    bw = 50 + int(b * 451)
+    return f"banded{n}_{bw}", matgen.banded(n, bw, seed=3000 + i)
 
 
 _GPU_LOCK = None
@@ -121,6 +183,81 @@ def _sweep_one(args):
     return i, name, feats, times
 
 
+def _sweep_one_v2(args):
+    """Worker: every point of GRID_V2 for matrix i, timed with both executors
+    (depth-1 points share one schedule across eps_1, which stage 0 ignores)."""
+    i, count, reps = args
+    import torch
+    from . import race_set_launch, race_upload, symm_spmv
+    name, m = dataset_matrix_v2(i, count)
+    feats = race_features(m)
+    out = {k: np.zeros(len(GRID_V2)) for k in V2_LAUNCH}
+    with _GPU_LOCK:
+        xd = torch.rand(m["n"], dtype=torch.float64, device="cuda:0")
+        bd = torch.empty_like(xd)
+        torch.cuda.synchronize()
+    done = {}
+    for j, (e0, e1, d) in enumerate(GRID_V2.points):
+        key = (e0, e1 if d != 1 else None, d)
+        if key in done:
+            for k in V2_LAUNCH:
+                out[k][j] = out[k][done[key]]
+            continue
+        done[key] = j
+        s = race_build(m, SWEEP_WORKERS_V2, eps=(e0, e1, 0.5), max_depth=d, host_only=True, windows=False)
+        with _GPU_LOCK:
+            race_upload(s)
+            for k, launch in V2_LAUNCH.items():
+                race_set_launch(s, 0, **launch)
+                # one timed call sizes the repetitions: about 1 ms of work per point,
+                # at least `reps` calls, so that short kernels are not launch noise
+                e_a = torch.cuda.Event(enable_timing=True)
+                e_b = torch.cuda.Event(enable_timing=True)
+                symm_spmv(s, xd, bd)
+                e_a.record()
+                symm_spmv(s, xd, bd)
+                e_b.record()
+                torch.cuda.synchronize()
+                one = max(1e-6, e_a.elapsed_time(e_b) * 1e-3)
+                r = int(min(400, max(reps, 1e-3 / one)))
+                e_a = torch.cuda.Event(enable_timing=True)
+                e_b = torch.cuda.Event(enable_timing=True)
+                e_a.record()
+                for _ in range(r):
+                    symm_spmv(s, xd, bd)
+                e_b.record()
+                torch.cuda.synchronize()
+                out[k][j] = e_a.elapsed_time(e_b) * 1e-3 / r
+            s.free()
+    return i, name, feats, out
+
+
+def sweep_v2(count=500, out_path=None, log=sys.stderr, workers=None, reps=6):
+    """Full-size sweep over GRID_V2 with both executors; saves features, times."""
+    import multiprocessing as mp
+    workers = workers or min(16, os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    lock = ctx.Lock()
+    feats = np.zeros((count, 16), np.float32)
+    times = {k: np.zeros((count, len(GRID_V2)), np.float64) for k in V2_LAUNCH}
+    names = [""] * count
+    t0 = time.time()
+    with ctx.Pool(workers, initializer=_init_worker, initargs=(lock,)) as pool:
+        for c, (i, name, f, t) in enumerate(pool.imap_unordered(_sweep_one_v2, [(i, count, reps) for i in range(count)])):
+            feats[i], names[i] = f, name
+            for k in V2_LAUNCH:
+                times[k][i] = t[k]
+            if c % 25 == 0:
+                print(f"sweep_v2 {c}/{count} {name} default best {t['default'].min()*1e6:.1f} us "
+                      f"leafcta best {t['leafcta'].min()*1e6:.1f} us  {time.time()-t0:.0f} s", file=log, flush=True)
+    out_path = out_path or os.path.join(DATA, "predictor_sweep_full.npz")
+    os.makedirs(os.path.dirname(out_path), exist_ok=True)
+    np.savez_compressed(out_path, features=feats, times_default=times["default"], times_leafcta=times["leafcta"],
+                        names=np.array(names), grid=np.array(GRID_V2.points, dtype=np.float64),
+                        workers=SWEEP_WORKERS_V2)
+    return feats, times, names
+
+
 def sweep(count=500, out_path=None, log=sys.stderr, workers=None, reps=2):
     """Exhaustive grid sweep on the GPU; returns and saves features, times."""
     import multiprocessing as mp
@@ -154,9 +291,10 @@ def split(n, seed=7, n_test=100):
 class Predictor:
     """The perceptron on the GPU: packed FP32 parameters + Adam state."""
 
-    def __init__(self, seed=0, device="cuda:0"):
+    def __init__(self, seed=0, device="cuda:0", grid=None):
         import torch
         self.torch = torch
+        self.grid = grid or GRID_V1
         self.dev = torch.device(device)
         n = lib().race_mlp_param_count()
         rng = np.random.default_rng(seed)
@@ -217,7 +355,7 @@ class Predictor:
 
     def choose(self, F):
         """Grid points (eps_0, eps_1, depth) for feature rows F."""
-        return [decode(y) for y in self.predict(F)]
+        return [self.grid.decode(y) for y in self.predict(F)]
 
     def save(self, path):
         np.concatenate([self.mu, self.sd, self.params.cpu().numpy()]).astype(np.float32).tofile(path)
@@ -235,34 +373,65 @@ def regret(times, choice_idx):
     return times[np.arange(len(times)), choice_idx] / best - 1.0
 
 
-def evaluate(pred, feats, times):
-    """Mean and median regret of the predictor and of the paper's default point."""
+def best_fixed_point(times, grid=None):
+    """The single grid point with the least mean regret over the given
+    (training) matrices: the baseline a learned choice has to beat."""
+    r = times / times.min(1, keepdims=True) - 1.0
+    return (grid or GRID_V1).points[int(np.argmin(r.mean(0)))]
+
+
+def evaluate(pred, feats, times, fixed=None):
+    """Mean and median regret of the predictor, of the paper's default point
+    and (if given) of a fixed grid point chosen on the training matrices."""
+    g = pred.grid
     pts = pred.choose(feats)
-    idx = np.array([point_index(*p) for p in pts])
+    idx = np.array([g.index(*p) for p in pts])
     r_mlp = regret(times, idx)
-    r_def = regret(times, np.full(len(times), point_index(*PAPER_POINT)))
-    return {"mlp_mean": float(r_mlp.mean()), "mlp_median": float(np.median(r_mlp)),
-            "paper_mean": float(r_def.mean()), "paper_median": float(np.median(r_def)),
-            "mlp_hits": int(np.sum(r_mlp == 0.0)), "n": int(len(times))}
+    r_def = regret(times, np.full(len(times), g.index(*PAPER_POINT)))
+    out = {"mlp_mean": float(r_mlp.mean()), "mlp_median": float(np.median(r_mlp)),
+           "paper_mean": float(r_def.mean()), "paper_median": float(np.median(r_def)),
+           "mlp_hits": int(np.sum(r_mlp == 0.0)), "n": int(len(times))}
+    if fixed is not None:
+        r_fix = regret(times, np.full(len(times), g.index(*fixed)))
+        out.update({"fixed_point": list(fixed), "fixed_mean": float(r_fix.mean()),
+                    "fixed_median": float(np.median(r_fix))})
+    return out
 
 
-def labels(times):
+def labels(times, grid=None):
+    g = grid or GRID_V1
     best = times.argmin(1)
-    return np.stack([encode(*GRID[j]) for j in best])
+    return np.stack([g.encode(*g.points[j]) for j in best])
+
+
+def train_and_evaluate(feats, times, grid, seed=0, epochs=400):
+    """Train on the 400-matrix split, evaluate on the 100 held out (split
+    seed 7): the network, the paper's default and the best fixed point."""
+    tr, te = split(len(feats))
+    pred = Predictor(seed=seed, grid=grid)
+    hist = pred.fit(feats[tr], labels(times[tr], grid), epochs=epochs)
+    res = evaluate(pred, feats[te], times[te], best_fixed_point(times[tr], grid))
+    return pred, {"loss_first": hist[0], "loss_last": hist[-1], **res}
 
 
 def main(argv):
     if argv and argv[0] == "sweep":
         count = int(argv[1]) if len(argv) > 1 else 500
         sweep(count)
+    elif argv and argv[0] == "sweep_full":
+        count = int(argv[1]) if len(argv) > 1 else 500
+        sweep_v2(count)
     elif argv and argv[0] == "train":
         d = np.load(os.path.join(DATA, "predictor_sweep.npz"))
-        feats, times = d["features"], d["times"]
-        tr, te = split(len(feats))
-        pred = Predictor(seed=0)
-        hist = pred.fit(feats[tr], labels(times[tr]))
+        pred, res = train_and_evaluate(d["features"], d["times"], GRID_V1)
         pred.save(os.path.join(DATA, "predictor.f32"))
-        print({"loss_first": hist[0], "loss_last": hist[-1], **evaluate(pred, feats[te], times[te])})
+        print(res)
+    elif argv and argv[0] == "train_full":
+        d = np.load(os.path.join(DATA, "predictor_sweep_full.npz"))
+        for target in ("default", "leafcta"):
+            pred, res = train_and_evaluate(d["features"], d["times_" + target], GRID_V2)
+            pred.save(os.path.join(DATA, f"predictor_full_{target}.f32"))
+            print(target, res)
     else:
         print(__doc__)
 
