@@ -307,6 +307,30 @@ def measure_ceilings(R, dev, stream, timer):
                    "independent FP64 FMA chains per thread, 1024 threads per SM (best of 3)"}
 
 
+def reduction_paths(R, dev, stream, timed, n, m):
+    """How fast this GPU combines scattered FP64 contributions, five ways
+    (race_probe_reductions), over m targets drawn uniformly from n (random)
+    and over consecutive targets (sequential): the reductions at L2 that the
+    default executors use, the plain read-modify-write a conflict-free
+    schedule would permit, shared-memory and cluster-shared-memory atomics
+    (the on-chip windows), and bulk row reductions of 16 doubles."""
+    import torch
+    with torch.cuda.stream(stream):
+        pats = {"random": torch.randint(0, n, (m,), dtype=torch.int32, device=dev),
+                "sequential": torch.remainder(torch.arange(m, device=dev), n).to(torch.int32)}
+        t = torch.zeros(16 * n, dtype=torch.float64, device=dev)
+    names = ("l2_reduction", "plain_rmw", "shared_atomic", "cluster_shared_atomic", "bulk_row_reduction")
+    out = {"targets": n, "contributions": m}
+    for pat, idx in pats.items():
+        for mode, name in enumerate(names):
+            sec = timed(lambda i: R.race_probe_reductions(mode, idx, m, n - 1, t, 16 * n, stream), 3, 1) / 3
+            elems = m * (16 if mode == 4 else 1)
+            out[f"{name}_{pat}_g_per_s"] = elems / sec / 1e9
+    del pats, t
+    torch.cuda.empty_cache()
+    return out
+
+
 def roofline_block(nbytes, seconds, peak, peak_kind, load_gbs, traffic=None, overwrite_bytes=None):
     """HBM roofline of one launch: algorithmic bytes over its time against
     the measured copy peak (and the load-only bandwidth, the paper's range)."""
@@ -425,6 +449,19 @@ def run_ours(args):
     t_red, t_col = probe(0), probe(1)
     mpk = mpk_block(R, pm, s, n, nu, dev, stream, timed, args.steps, peak)
     R.race_set_launch(s, 0, **lc)
+    red_paths = reduction_paths(R, dev, stream, timed, n, nu - n) if not args.no_extra else None
+    spmm_head = None
+    if args.spmm_k:
+        # SymmSpMM on the headline schedule with the workload's launch (no tuning:
+        # the profiling recipe captures exactly this kernel)
+        k = args.spmm_k
+        with torch.cuda.stream(stream):
+            Xk = [torch.rand(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+            Bk = [torch.empty(n * k, dtype=torch.float64, device=dev) for _ in range(2)]
+        tk = timed(lambda i: R.symm_spmm(s, k, Xk[i % 2], Bk[i % 2], stream), args.steps, args.warmup) / args.steps
+        spmm_head = {"k": k, "ms_per_step": tk * 1e3, "gflops": pm.flops(nf, k) / tk / 1e9, "launch": lc,
+                     **spmm_roof(pm.flops(nf, k), pm.symm_bytes_rmw(n, nu, k), tk, peak, ceil["fp64_fma_per_s"])}
+        del Xk, Bk
     # ---- traffic baseline: full-CRS SpMV on the same permuted matrix -----------------------
     t_full = timed(lambda i: R.spmv_full(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     # ---- the conflict-free RACE executors (a few steps: they are slow) on the schedule that
@@ -438,6 +475,20 @@ def run_ours(args):
     t_win_race = timed(lambda i: R.symm_spmv_exec(s_cf, R.RACE_EXEC_WINDOW_RACE, xs[i % RING], bs[i % RING],
                                                   stream), 3, 1)
     s_cf.free()
+    # ---- the paper's comparison methods, multicolouring (MC) and algebraic block
+    # multicolouring (ABMC, blocks of 64 rows), under the same conflict-free executors --------
+    colourings = {}
+    if not args.no_extra:
+        for label, method, block in (("mc", R.RACE_COLOR_MC, 1), ("abmc64", R.RACE_COLOR_ABMC, 64)):
+            t0c = time.perf_counter()
+            sc = R.race_build_coloring(m, method, block, n_workers=cf["n_workers"], stream=stream, windows=False)
+            bsec = time.perf_counter() - t0c
+            ic = sc.info()
+            R.race_set_launch(sc, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
+            t_c = timed(lambda i: R.symm_spmv(sc, xs[i % RING], bs[i % RING], stream), 3, 1)
+            colourings[label] = {"colours": ic["n_phases"], "leaves": ic["n_leaves"], "eta": ic["eta"],
+                                 "leaf_cta_ms_per_step": t_c / 3 * 1e3, "build_seconds": bsec}
+            sc.free()
     # ---- the same two kernels on the input order (no RACE permutation) --------------------
     s_nat = R.race_build(m, cfg["n_workers"], natural_order=True, windows=False, stream=stream)
     R.race_set_launch(s_nat, 0, **lc)
@@ -584,11 +635,15 @@ def run_ours(args):
                                             "one_level_stage0": bool(cf.get("one_level_stage0", False)),
                                             "n_phases": info_cf["n_phases"], "n_leaves": info_cf["n_leaves"],
                                             "eta": info_cf["eta"]},
+                               "colourings": colourings,
                                "what": "RACE_EXEC_LEAF_CTA and RACE_EXEC_WINDOW_RACE (phase by phase, no two concurrent "
                                        "leaves share an entry of b; x and b in that schedule's order) on a fully "
-                                       "recursed schedule, 3 steps each"},
+                                       "recursed schedule, 3 steps each; the same leaf executor on the in-house MC "
+                                       "and ABMC colourings (race_build_coloring)"},
         "speedup_vs_full": t_full / t_symm,
         "matrix_powers": mpk,
+        "reduction_paths": red_paths,
+        "spmm_headline": spmm_head,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
                 "how": "per step: pinned H2D of x, permute, SymmSpMV, unpermute, D2H of b into pinned memory; "
@@ -980,6 +1035,8 @@ def build_parser():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="measure the headline workload only (no stencil, Anderson and batch blocks)")
+    ap.add_argument("--spmm-k", type=int, default=0,
+                    help="also time SymmSpMM with this many right-hand sides on the headline schedule")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     return ap

@@ -169,6 +169,30 @@ void race_default_params(race_params *p, int32_t n_workers);
  * _UNSUPPORTED (dist_k other than 2), _OVERFLOW, _NOMEM, _CUDA.            */
 int race_build(const race_csr_upper *a, const race_params *p, void *stream, race_schedule **out);
 
+/* race_build_coloring — the multicolouring schedules the paper compares
+ * RACE with (Sec. 3.3, Sec. 6.3), built in-house from its description:
+ *   RACE_COLOR_MC:   every row is a unit;
+ *   RACE_COLOR_ABMC: units are blocks of block_rows consecutive rows of the
+ *                    (RCM-relabelled, with RACE_FLAG_RCM) input order -- the
+ *                    partitioning step, for which the paper uses METIS and a
+ *                    block size from a scan over 4..128 -- 1 <= block_rows <=
+ *                    4096.
+ * Units are coloured first fit in index order: a unit takes the smallest
+ * colour no earlier unit within distance 2 of it (in the symmetric graph)
+ * holds, so the rows of one colour never share an entry of b (the
+ * distance-2 condition of Sec. 4.2).  The permutation lists the units colour
+ * by colour; each colour is a phase and each unit a leaf, so every executor
+ * and entry point serves the result like a RACE schedule (race_get_info
+ * reports one tree node; eta = N / (N_eff N_t) with N_eff the sum over
+ * phases of their longest leaf, at most 1).  n_workers: N_t for eta.
+ * flags: RACE_FLAG_HOST_ONLY, RACE_FLAG_NO_WINDOWS, RACE_FLAG_RCM.
+ * Errors as race_build; RACE_ERR_INVALID also for an unknown method or a
+ * block size out of range.                                                */
+#define RACE_COLOR_MC 0
+#define RACE_COLOR_ABMC 1
+int race_build_coloring(const race_csr_upper *a, int32_t method, int32_t block_rows, int32_t n_workers, uint32_t flags,
+                        void *stream, race_schedule **out);
+
 /* race_upload — turns a schedule built with RACE_FLAG_HOST_ONLY into a
  * device schedule (uploads it on `stream`, returns after the copies have
  * completed); no-op for a device schedule.  Lets callers build schedules on
@@ -325,6 +349,26 @@ int race_probe_scatter(const race_schedule *s, int32_t mode, double *b_d, void *
  * Errors: RACE_ERR_INVALID (bad what, n < 0, misaligned input, iters < 1),
  * _UNSUPPORTED (more than 4096 blocks), _CUDA.                            */
 int race_probe_peaks(int32_t what, const double *in_d, int64_t n, double *out_d, int32_t iters, void *stream);
+
+/* race_probe_reductions — diagnostic, computes nothing of SymmSpMV: the ways
+ * the contributions of the transposed update (Alg. "SymmSpMV": b[j] +=
+ * a_ij x_i) can be combined on this GPU, each timed over the same m target
+ * indices idx_d[0, m) (device int32, clamped to [0, max_index]):
+ *   mode 0: reduction at L2 (red.global.add.f64), target[idx[i]] += 1;
+ *   mode 1: plain load, add and store of target[idx[i]], as a
+ *           conflict-free schedule would allow (repeated indices race);
+ *   mode 2: FP64 atomic add into the block's shared memory, slot
+ *           idx[i] mod 4096;
+ *   mode 3: the same into the shared memory of the other block of a
+ *           two-block cluster (distributed shared memory);
+ *   mode 4: bulk reduction of a 16-double row from shared memory into
+ *           target[16 idx[i] .. 16 idx[i] + 15] (cp.reduce.async.bulk).
+ * target_d: device doubles, 16-byte aligned, n_target at least max_index + 1
+ * (16 (max_index + 1) for mode 4; and at least 8 per SM for modes 2 and 3,
+ * whose blocks store one value each at the end).  Grid: 8 blocks of 256
+ * threads per SM.  Errors: RACE_ERR_INVALID, _CUDA.                       */
+int race_probe_reductions(int32_t mode, const int32_t *idx_d, int64_t m, int32_t max_index, double *target_d,
+                          int64_t n_target, void *stream);
 
 /* race_poll_status — synchronises `stream`, then returns RACE_ERR_TIMEOUT
  * (and clears it) if a bounded device wait of this schedule's kernels gave

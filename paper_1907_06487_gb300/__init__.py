@@ -50,7 +50,8 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "symm_spmv_noalloc", "race_batch_create", "race_batch_launch", "race_batch_free", "race_autotune",
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
             "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz",
-            "race_probe_wait_timeout", "race_probe_peaks", "race_matrix_powers")
+            "race_probe_wait_timeout", "race_probe_peaks", "race_matrix_powers", "race_probe_reductions",
+            "race_build_coloring")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -120,6 +121,9 @@ def lib():
     L.race_default_params.argtypes = [ctypes.POINTER(race_params), i32]
     L.race_default_params.restype = None
     L.race_build.argtypes = [ctypes.POINTER(race_csr_upper), ctypes.POINTER(race_params), vp, ctypes.POINTER(vp)]
+    L.race_build_coloring.argtypes = [ctypes.POINTER(race_csr_upper), i32, i32, i32, ctypes.c_uint32, vp,
+                                      ctypes.POINTER(vp)]
+    L.race_build_coloring.restype = ctypes.c_int
     for name in ("symm_spmv", "spmv_full"):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.symm_spmm.argtypes = [vp, i32, vp, vp, vp]
@@ -144,6 +148,8 @@ def lib():
     L.race_poll_status.argtypes = [vp, vp]
     L.race_poll_status.restype = ctypes.c_int
     L.race_probe_peaks.argtypes = [i32, vp, ctypes.c_int64, vp, i32, vp]
+    L.race_probe_reductions.argtypes = [i32, vp, ctypes.c_int64, i32, vp, ctypes.c_int64, vp]
+    L.race_probe_reductions.restype = ctypes.c_int
     L.race_matrix_powers.argtypes = [vp, i32, vp, vp, i32, vp]
     L.race_matrix_powers.restype = ctypes.c_int
     L.race_probe_peaks.restype = ctypes.c_int
@@ -318,6 +324,24 @@ def race_build(m, n_workers, eps=PAPER_EPS, max_depth=-1, balance=RACE_BAL_ROWS,
     return Schedule(h.value, a.n)
 
 
+RACE_COLOR_MC = 0
+RACE_COLOR_ABMC = 1
+
+
+def race_build_coloring(m, method, block_rows=1, n_workers=152, host_only=False, stream=None, val_type=RACE_F64,
+                        windows=True, rcm=False) -> Schedule:
+    """race_build_coloring: the MC (rows) or ABMC (blocks of block_rows rows)
+    multicolouring schedule of a matrix dict, one phase per colour."""
+    a, keep = _csr(m, val_type)
+    flags = ((RACE_FLAG_HOST_ONLY if host_only else 0) | (0 if windows else RACE_FLAG_NO_WINDOWS) |
+             (RACE_FLAG_RCM if rcm else 0))
+    h = ctypes.c_void_p()
+    _check(lib().race_build_coloring(ctypes.byref(a), int(method), int(block_rows), int(n_workers), flags,
+                                     _stream(stream), ctypes.byref(h)), "race_build_coloring")
+    del keep
+    return Schedule(h.value, a.n)
+
+
 def race_import(m, image: bytes, host_only=False, stream=None, val_type=RACE_F64, windows=True) -> Schedule:
     """race_import: the schedule of a race_export image, on the matrix it was built from."""
     a, keep = _csr(m, val_type)
@@ -382,6 +406,13 @@ def race_probe_peaks(what, inp, n, out, iters=1, stream=None):
     bandwidth), what 1 runs FP64 fused multiply-add chains (iters each)."""
     _check(lib().race_probe_peaks(int(what), _ptr(inp), int(n), _ptr(out), int(iters), _stream(stream)),
            "race_probe_peaks")
+
+
+def race_probe_reductions(mode, idx, m, max_index, target, n_target, stream=None):
+    """Diagnostic: one way of combining scattered contributions (mode 0..4)
+    over the target indices idx[0, m)."""
+    _check(lib().race_probe_reductions(int(mode), _ptr(idx), int(m), int(max_index), _ptr(target), int(n_target),
+                                       _stream(stream)), "race_probe_reductions")
 
 
 def race_probe_wait_timeout(s: Schedule, x, b, stream=None):

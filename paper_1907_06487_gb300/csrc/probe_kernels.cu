@@ -14,6 +14,7 @@
 // block (race_device_sms() * 4 <= 4096 on any current GPU).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 
@@ -101,6 +102,126 @@ extern "C" int race_probe_peaks(int32_t what, const double* in_d, int64_t n, dou
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         race_set_detail(std::string("race_probe_peaks: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
+    }
+    return RACE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// race_probe_reductions: the ways a GPU can combine the transposed update's
+// contributions to one entry of b, timed on the same stream of target
+// indices (the measurements behind the executors' use of reductions at L2):
+//   mode 0: reduction at L2, red.global.add.f64 target[idx[i]] += 1;
+//   mode 1: plain load, add and store of target[idx[i]] (what a
+//           conflict-free schedule allows; indices that repeat race);
+//   mode 2: FP64 atomic add in the block's shared memory, slot idx[i] % 4096;
+//   mode 3: FP64 atomic add in the shared memory of the other block of a
+//           two-block cluster (distributed shared memory), same slots;
+//   mode 4: bulk reduction (cp.reduce.async.bulk .add.f64) of a 16-double
+//           row from shared memory into target[16 idx[i] .. 16 idx[i] + 15].
+// Modes 2 and 3 store each block's slot 0 into target[block] at the end.
+// ---------------------------------------------------------------------------
+namespace race_probe {
+
+// indices are clamped to [0, hi] so that a wrong index array cannot leave the target
+__device__ __forceinline__ int64_t clamp_index(int32_t v, int32_t hi) {
+    return static_cast<int64_t>(min(static_cast<uint32_t>(v), static_cast<uint32_t>(hi)));
+}
+
+__global__ void __launch_bounds__(kThreads) k_red_global(const int32_t* __restrict__ idx, int64_t m, int32_t hi,
+                                                         double* t) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * kThreads)
+        atomicAdd(t + clamp_index(__ldg(idx + i), hi), 1.0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_rmw_global(const int32_t* __restrict__ idx, int64_t m, int32_t hi,
+                                                         double* t) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * kThreads) {
+        const int64_t c = clamp_index(__ldg(idx + i), hi);
+        t[c] = t[c] + 1.0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_red_shared(const int32_t* __restrict__ idx, int64_t m, double* t) {
+    __shared__ double s[4096];
+    for (int i = threadIdx.x; i < 4096; i += kThreads) s[i] = 0.0;
+    __syncthreads();
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * kThreads)
+        atomicAdd(s + (__ldg(idx + i) & 4095), 1.0);
+    __syncthreads();
+    if (threadIdx.x == 0) t[blockIdx.x] = s[0];
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads)
+    k_red_cluster(const int32_t* __restrict__ idx, int64_t m, double* t) {
+    __shared__ double s[4096];
+    for (int i = threadIdx.x; i < 4096; i += kThreads) s[i] = 0.0;
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    uint32_t rank, remote;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(remote)
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(s))), "r"(rank ^ 1u));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * kThreads) {
+        const uint32_t a = remote + static_cast<uint32_t>(__ldg(idx + i) & 4095) * 8u;
+        asm volatile("red.shared::cluster.add.f64 [%0], %1;" ::"r"(a), "d"(1.0) : "memory");
+    }
+    // the peer's adds into this block's array finish before either block leaves
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (threadIdx.x == 0) t[blockIdx.x] = s[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_bulk_rows(const int32_t* __restrict__ idx, int64_t m, int32_t hi,
+                                                        double* t) {
+    __shared__ __align__(128) double s[kThreads][16];
+    for (int c = 0; c < 16; ++c) s[threadIdx.x][c] = 1.0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(&s[threadIdx.x][0]));
+    int pend = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; i < m;
+         i += static_cast<int64_t>(gridDim.x) * kThreads) {
+        double* dst = t + clamp_index(__ldg(idx + i), hi) * 16;
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], 128;" ::"l"(dst), "r"(sa)
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        if (++pend >= 8) {
+            asm volatile("cp.async.bulk.wait_group.read 4;" ::: "memory");
+            pend = 4;
+        }
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+}  // namespace race_probe
+
+extern "C" int race_probe_reductions(int32_t mode, const int32_t* idx_d, int64_t m, int32_t max_index, double* target_d,
+                                     int64_t n_target, void* stream) {
+    const int grid = race_device_sms() * 8;  // even: whole clusters of two
+    const int64_t need = mode == 4 ? 16 * (static_cast<int64_t>(max_index) + 1)
+                                   : (mode == 2 || mode == 3 ? std::max<int64_t>(grid, max_index + 1)
+                                                             : static_cast<int64_t>(max_index) + 1);
+    if (mode < 0 || mode > 4 || !idx_d || !target_d || m < 0 || max_index < 0 || n_target < need ||
+        (reinterpret_cast<uintptr_t>(target_d) & 15u)) {
+        race_set_detail("race_probe_reductions: bad mode, NULL, or a target array too small for the indices "
+                        "(16 (max_index + 1) doubles for mode 4; at least one per block for modes 2 and 3)");
+        return RACE_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (mode) {
+        case 0: race_probe::k_red_global<<<grid, race_probe::kThreads, 0, st>>>(idx_d, m, max_index, target_d); break;
+        case 1: race_probe::k_rmw_global<<<grid, race_probe::kThreads, 0, st>>>(idx_d, m, max_index, target_d); break;
+        case 2: race_probe::k_red_shared<<<grid, race_probe::kThreads, 0, st>>>(idx_d, m, target_d); break;
+        case 3: race_probe::k_red_cluster<<<grid, race_probe::kThreads, 0, st>>>(idx_d, m, target_d); break;
+        default: race_probe::k_bulk_rows<<<grid, race_probe::kThreads, 0, st>>>(idx_d, m, max_index, target_d); break;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("race_probe_reductions: ") + cudaGetErrorString(e));
         return RACE_ERR_CUDA;
     }
     return RACE_OK;

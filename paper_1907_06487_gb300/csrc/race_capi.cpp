@@ -417,6 +417,49 @@ int race_build(const race_csr_upper* a, const race_params* p, void* stream, race
     return finish_schedule(s, a->val_type, p->group_lanes, p->flags, stream, out);
 }
 
+int race_build_coloring(const race_csr_upper* a, int32_t method, int32_t block_rows, int32_t n_workers, uint32_t flags,
+                        void* stream, race_schedule** out) {
+    if (!out) return fail(RACE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!a) return fail(RACE_ERR_INVALID, "NULL argument");
+    int rc = check_matrix(a);
+    if (rc != RACE_OK) return rc;
+    if (method != RACE_COLOR_MC && method != RACE_COLOR_ABMC) return fail(RACE_ERR_INVALID, "unknown colouring method");
+    if (method == RACE_COLOR_ABMC && (block_rows < 1 || block_rows > 4096))
+        return fail(RACE_ERR_INVALID, "block_rows must be in 1..4096");
+    if (n_workers < 1) return fail(RACE_ERR_INVALID, "n_workers < 1");
+    if (flags & ~(RACE_FLAG_HOST_ONLY | RACE_FLAG_NO_WINDOWS | RACE_FLAG_RCM))
+        return fail(RACE_ERR_INVALID, "race_build_coloring takes RACE_FLAG_HOST_ONLY, _NO_WINDOWS and _RCM");
+    race_params p;
+    race_default_params(&p, n_workers);
+    race_schedule* s = new (std::nothrow) race_schedule();
+    if (!s) return fail(RACE_ERR_NOMEM, "host allocation");
+    try {
+        std::vector<int32_t> rp, col;
+        std::vector<double> val;
+        rc = canonicalize(a, rp, col, val);
+        if (rc != RACE_OK) {
+            delete s;
+            return rc;
+        }
+        if (flags & RACE_FLAG_RCM) {
+            const std::vector<int32_t> order = race::rcm_order(a->n, rp.data(), col.data());
+            std::vector<int32_t> rp1, col1;
+            std::vector<double> val1;
+            permute_upper(a->n, rp, col, val, order, rp1, col1, val1);
+            race::coloring_plan(a->n, rp1.data(), col1.data(), method, block_rows, p, s->plan);
+            for (int32_t& v : s->plan.perm) v = order[static_cast<size_t>(v)];
+        } else {
+            race::coloring_plan(a->n, rp.data(), col.data(), method, block_rows, p, s->plan);
+        }
+        permute_upper(a->n, rp, col, val, s->plan.perm, s->h_rp, s->h_col, s->h_val64);
+    } catch (const std::bad_alloc&) {
+        delete s;
+        return fail(RACE_ERR_NOMEM, "host allocation during build");
+    }
+    return finish_schedule(s, a->val_type, 0, flags, stream, out);
+}
+
 int race_import(const race_csr_upper* a, const void* image, size_t size, uint32_t flags, void* stream,
                 race_schedule** out) {
     if (!out) return fail(RACE_ERR_INVALID, "out is NULL");

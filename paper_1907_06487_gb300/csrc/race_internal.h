@@ -47,6 +47,11 @@ void build_plan(int32_t n, const int32_t* row_ptr, const int32_t* col, const rac
 // holding one leaf with every row.
 void natural_plan(int32_t n, const race_params& p, Plan& out);
 
+// The MC / ABMC schedules of race_build_coloring (coloring.cpp): one phase
+// per colour, one leaf per unit (a row, or a block of block_rows rows).
+void coloring_plan(int32_t n, const int32_t* rp, const int32_t* col, int32_t method, int32_t block_rows,
+                   const race_params& p, Plan& out);
+
 // Canonical export image (layout documented in race.h).
 std::vector<uint8_t> export_plan(const Plan& plan);
 

@@ -45,3 +45,39 @@ def test_fma_chains_and_refusals(dev):
         with pytest.raises(R.RaceError) as e:
             R.race_probe_peaks(*args)
         assert e.value.code == R.RACE_ERR_INVALID
+
+
+def test_reduction_paths_count_every_contribution(dev):
+    """race_probe_reductions: reductions at L2 and bulk row reductions count
+    every index exactly; a plain read-modify-write does too when no index
+    repeats; the shared and cluster-shared atomics lose none (all indices on
+    slot 0: the blocks' slot-0 totals sum to m)."""
+    rng = np.random.default_rng(3)
+    n, m = 5000, 200000
+    idx = rng.integers(0, n, m).astype(np.int32)
+    idx_d = torch.from_numpy(idx).to(dev)
+    want = np.bincount(idx, minlength=n).astype(np.float64)
+    t = torch.zeros(16 * n, dtype=torch.float64, device=dev)
+    R.race_probe_reductions(0, idx_d, m, n - 1, t, n)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy()[:n], want)
+    t.zero_()
+    R.race_probe_reductions(4, idx_d, m, n - 1, t, 16 * n)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy().reshape(n, 16), np.repeat(want[:, None], 16, 1))
+    perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).to(dev)
+    t.zero_()
+    R.race_probe_reductions(1, perm, n, n - 1, t, n)
+    torch.cuda.synchronize()
+    assert np.all(t.cpu().numpy()[:n] == 1.0)
+    zeros = torch.zeros(m, dtype=torch.int32, device=dev)
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    for mode in (2, 3):
+        t.zero_()
+        R.race_probe_reductions(mode, zeros, m, n - 1, t, max(n, blocks))
+        torch.cuda.synchronize()
+        assert float(t[:blocks].sum()) == float(m), mode
+    with pytest.raises(R.RaceError):
+        R.race_probe_reductions(4, idx_d, m, n - 1, t, n)  # target too small for rows of 16
+    with pytest.raises(R.RaceError):
+        R.race_probe_reductions(5, idx_d, m, n - 1, t, n)
