@@ -309,10 +309,12 @@ typedef struct {
                                 per lane and step of RACE_EXEC_DF64_RED
                                 (4, or 8 when >= 8)                         */
     int32_t fp64_quarters;   /* RACE_EXEC_DF64_RED (and its SymmSpMM): in
-                                this many quarters of the warps (0..4) the
-                                transposed updates use FP64 multiplies, in
-                                the rest double-float arithmetic; shares the
-                                work between the FP64 and integer pipes  */
+                                this many of every four row iterations of a
+                                warp (0..4) the transposed updates use FP64
+                                multiplies, in the rest double-float
+                                arithmetic; shares the work between the
+                                FP64 and integer pipes, spread evenly over
+                                each SM's four FP64 units                */
     int32_t rowsum_fp64_quarters; /* RACE_EXEC_STAGED: in this many quarters
                                 of the warps (0..4) the row sums are FP64
                                 multiply-adds, in the rest double-float
@@ -529,7 +531,8 @@ void race_batch_free(race_batch *b);
 /* race_autotune — times the candidate launch shapes (executors
  * RACE_EXEC_ROWS_RED, RACE_EXEC_PIPE_RED and, when the matrix's values are
  * in its range, RACE_EXEC_DF64_RED, with their lane, row and register
- * shapes, default and 4 blocks per SM) of symm_spmv (k == 1) or
+ * shapes, default and 4 blocks per SM, and 6 blocks per SM with 1 or 2
+ * FP64 quarters for RACE_EXEC_DF64_RED) of symm_spmv (k == 1) or
  * symm_spmm (k > 1) on the given buffers: one warm-up and `reps` timed
  * calls each, CUDA events on `stream`.  Keeps the fastest as the
  * schedule's launch shape and returns it in *best (and its time per call

@@ -42,11 +42,13 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # phases, leaf-per-CTA executor 0.996 -> 0.741 ms).  `sweeps` is the schedule
 # of the Gauss-Seidel and Kaczmarz sweeps (distance-2 phases throughout: the
 # Kaczmarz update writes every column of a row).
-# (XXZ L=26 sweep of blocks per SM x entries per step x FP64 share: 6 blocks of
-# 40-register threads, 4 entries, half the warps' transposed products in FP64
-# lead, 0.322 ms against 0.328 at 5 blocks and 0.330-0.345 at shares 1 and 0)
+# (sweeps of blocks per SM x entries per step x FP64 share on GB300: XXZ L=26
+# 6 blocks of 40-register threads, 4 entries, half of the row groups'
+# transposed products in FP64, 0.321 ms against 0.322-0.328 at 5 blocks or
+# share 1/4 and 0.348 at share 0; the 27-point stencil 4 blocks, 4 entries,
+# share 2/4, 0.366 ms against 0.372 at 8 entries per step)
 _L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=6, regs_per_row=4, fp64_quarters=2)
-_LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=8, fp64_quarters=2)
+_LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=4, fp64_quarters=2)
 _F = dict(executor=2, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=16)
 SCHEDULE = {
     "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),

@@ -28,6 +28,7 @@
 #include <string>
 
 #include "df64.cuh"
+#include "fp64_share.cuh"
 #include "race_internal.h"
 
 namespace {
@@ -106,14 +107,14 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
                                                      const double* __restrict__ x, double* b, int fp64_quarters) {
     const int lane = threadIdx.x & (G - 1);
     const unsigned mask = lane_mask<G>();
-    // warps in the first fp64_quarters quarters scatter with FP64 multiplies
-    // (warp-uniform), sharing the work between the FP64 and integer pipes
-    const bool warp64 = ((static_cast<int>(blockIdx.x) * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5)) & 3) <
-                        fp64_quarters;
+    // fp64_quarters of every four warp-wide row groups scatter with FP64
+    // multiplies (warp-uniform, spread over the SM's FP64 units), the rest in
+    // double-float: the work is shared between the FP64 and integer pipes
     const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
     for (int64_t r = gid; r < n; r += ngroups) {
         const int32_t row = static_cast<int32_t>(r);
+        const bool warp64 = fp64_group(static_cast<uint32_t>(static_cast<uint64_t>(r) / (32 / G)), fp64_quarters);
         const int32_t lo = __ldg(rp + row), hi = __ldg(rp + row + 1);
         const double xr = __ldg(x + row);
         float xrh, xrl;

@@ -16,6 +16,7 @@
 #include <cstdint>
 
 #include "df64.cuh"
+#include "fp64_share.cuh"
 #include "race_internal.h"
 
 namespace {
@@ -426,12 +427,12 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
                                                             const VT* __restrict__ val, const double* __restrict__ X,
                                                             double* B, int fp64_quarters) {
     const int c = threadIdx.x & (K - 1);
-    // warps in the first fp64_quarters quarters scatter in FP64 (warp-uniform)
-    const bool warp64 = ((static_cast<int>(blockIdx.x) * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5)) & 3) <
-                        fp64_quarters;
+    // fp64_quarters of every four warp-wide row groups scatter in FP64
+    // (warp-uniform, spread over the SM's FP64 units)
     const int64_t grp = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / K;
     const int64_t ngrp = static_cast<int64_t>(gridDim.x) * kBlock / K;
     for (int64_t r0 = grp; r0 < n; r0 += ngrp * R) {
+        const bool warp64 = fp64_group(static_cast<uint32_t>(static_cast<uint64_t>(r0) / (32 / K)), fp64_quarters);
         int32_t js[R], je[R];
         double xr[R], acc[R];
         float xrh[R], xrl[R];
@@ -557,20 +558,20 @@ __device__ __forceinline__ double mm_row_df(int32_t js, int32_t je, int c, const
 
 // SymmSpMM with double-float transposed products, one row per group of K
 // lanes (lane c owns right-hand side c) and rows strided over the grid.  The
-// lane's mode for the row: x_r outside the split's range or a warp of the
-// FP64 share (warp-uniform, the first fp64_quarters of every four warps):
-// FP64 multiplies; x_r zero: no transposed updates; else double-float.
+// lane's mode for the row: x_r outside the split's range or a row group of
+// the FP64 share (warp-uniform, fp64_quarters of every four, spread over the
+// SM's FP64 units): FP64 multiplies; x_r zero: no transposed updates; else
+// double-float.
 template <typename VT, int K>
-__global__ void __launch_bounds__(kBlock) k_symm_mm_rows_df(int32_t n, const int32_t* __restrict__ rp,
+__global__ void __launch_bounds__(kBlock, 6) k_symm_mm_rows_df(int32_t n, const int32_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
                                                            const VT* __restrict__ val, const double* __restrict__ X,
                                                            double* B, int fp64_quarters) {
     const int c = threadIdx.x & (K - 1);
-    const bool warp64 = ((static_cast<int>(blockIdx.x) * (kBlock / 32) + static_cast<int>(threadIdx.x >> 5)) & 3) <
-                        fp64_quarters;
     const int64_t grp = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / K;
     const int64_t ngrp = static_cast<int64_t>(gridDim.x) * kBlock / K;
     for (int64_t r = grp; r < n; r += ngrp) {
+        const bool warp64 = fp64_group(static_cast<uint32_t>(static_cast<uint64_t>(r) / (32 / K)), fp64_quarters);
         const int32_t js = __ldg(rp + r), je = __ldg(rp + r + 1);
         const double xr = __ldg(X + r * K + c);
         float xrh, xrl;

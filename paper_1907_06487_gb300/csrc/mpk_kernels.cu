@@ -31,8 +31,8 @@
 //                       blocks) fits there.
 //
 // Arithmetic as RACE_EXEC_DF64_RED: FP64 row sums; the transposed products
-// in FP64 in fp64_quarters / 4 of the warps and in double-float in the rest
-// (relative error below 2^-44 each).  The columns of Y are read through L2
+// in FP64 in fp64_quarters / 4 of each warp's row groups and in double-float
+// in the rest (relative error below 2^-44 each).  The columns of Y are read through L2
 // only (ld.global.cg): they are written by reductions during the launch.
 // Every wait on a done flag is bounded; one that gives up records
 // RACE_ERR_TIMEOUT in the schedule's status word and its block leaves the
@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "df64.cuh"
+#include "fp64_share.cuh"
 #include "race_internal.h"
 
 namespace race_mpk {
@@ -129,7 +130,6 @@ __global__ void __launch_bounds__(kThreads) k_mpk_wave(int32_t n, const int32_t*
     int32_t* done = flags + 2 + p;
     const long long total = (static_cast<long long>(nblk) + static_cast<long long>(p - 1) * step) * p;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool tp64 = ((static_cast<int>(blockIdx.x) * (kThreads / 32) + warp) & 3) < fp64_quarters;
     for (;;) {
         if (threadIdx.x == 0) s_ticket = static_cast<long long>(atomicAdd(ctr, 1ull));
         __syncthreads();
@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(kThreads) k_mpk_wave(int32_t n, const int32_t*
         double* dst = Y + static_cast<long long>(q) * n;
         const int32_t r0 = t * rows, r1 = min(n, r0 + rows);
         for (int32_t base = r0 + warp * 32; base < r1; base += kThreads)
-            warp_rows<B>(base + lane, base + lane < r1, rp, col, val, src, dst, tp64);
+            warp_rows<B>(base + lane, base + lane < r1, rp, col, val, src, dst,
+                         fp64_group(static_cast<uint32_t>(base >> 5) + static_cast<uint32_t>(q), fp64_quarters));
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) st_release(done + static_cast<long long>(q) * nblk + t, 1);

@@ -306,7 +306,11 @@ __global__ void __launch_bounds__(kThreads) k_symm_staged(int32_t n, const int32
     const int64_t gw = static_cast<int64_t>(blockIdx.x) * kWarps + w;
     const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarps;
     if (gw >= ntiles) return;
-    const int quarter = static_cast<int>(gw & 3);
+    // the warp's quarter (fixed for its whole loop): every four consecutive
+    // warps take all four, and the warps an SM deals to one sub-partition
+    // (same gw mod 4) cycle through them, so each sub-partition's FP64 unit
+    // gets its share
+    const int quarter = static_cast<int>((gw + (gw >> 2)) & 3);
     const bool rs64 = quarter < rs64_quarters;
     const bool tp64 = 3 - quarter < tp64_quarters;
 #define RACE_STG_LOOP(R, T) \
