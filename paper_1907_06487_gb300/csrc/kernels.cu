@@ -808,7 +808,7 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
             case 4: RACE_MM_ROWS(4); break;
             case 8: RACE_MM_ROWS(8); break;
             case 16: RACE_MM_ROWS(16); break;
-            default: return RACE_ERR_UNSUPPORTED;
+            default: race_set_detail("k must be 1, 2, 4, 8 or 16"); return RACE_ERR_UNSUPPORTED;
         }
 #undef RACE_MM_ROWS
 #undef RACE_MM_ROWS_DF
@@ -820,7 +820,7 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
         case 4: launch_mm<VT, 4>(s, X, B, st); break;
         case 8: launch_mm<VT, 8>(s, X, B, st); break;
         case 16: launch_mm<VT, 16>(s, X, B, st); break;
-        default: return RACE_ERR_UNSUPPORTED;
+        default: race_set_detail("k must be 1, 2, 4, 8 or 16"); return RACE_ERR_UNSUPPORTED;
     }
     return RACE_OK;
 }
@@ -916,10 +916,7 @@ int symm_spmm(const race_schedule* s, int32_t k, const double* X_d, double* B_d,
         return RACE_ERR_CUDA;
     }
     rc = s->val_type == RACE_F64 ? launch_mm_k<double>(s, k, X_d, B_d, st) : launch_mm_k<float>(s, k, X_d, B_d, st);
-    if (rc) {
-        race_set_detail("k must be 1, 2, 4, 8 or 16");
-        return rc;
-    }
+    if (rc) return rc;  // the detail is set where the error arose
     return check_launch("symm_spmm");
 }
 

@@ -166,11 +166,19 @@ def test_degenerate(dev, oracle_mod, matgen_mod, exe):
 
 @pytest.mark.parametrize("k", [2, 4, 8, 16])
 @pytest.mark.parametrize("rows_in_flight", [1, 4])
-def test_spmm_double_float_scatter(dev, oracle_mod, matgen_mod, k, rows_in_flight):
+@pytest.mark.parametrize("val_type", ["f64", "f32"])
+def test_spmm_double_float_scatter(dev, oracle_mod, matgen_mod, k, rows_in_flight, val_type):
     m = matgen_mod.stencil3d(14, npt=27, seed=6)
-    s = R.race_build(m, 32)
+    m = dict(m, val=m["val"].copy())
+    rows = np.repeat(np.arange(m["n"]), np.diff(m["row_ptr"]))
+    m["val"][np.flatnonzero(m["col"] != rows)[::11]] = 0.0  # explicit zeros scatter nothing
+    vt = R.RACE_F64
+    if val_type == "f32":
+        m["val"] = m["val"].astype(np.float32).astype(np.float64)
+        vt = R.RACE_F32
+    s = R.race_build(m, 32, val_type=vt)
     R.race_set_launch(s, 0, executor=DF, group_lanes=1, rows_per_group=rows_in_flight, blocks_per_sm=0,
-                      regs_per_row=4)
+                      regs_per_row=4, fp64_quarters=1)
     n = m["n"]
     X = matgen_mod.uniform(n * k, 14, -1.0, 1.0).reshape(n, k)
     X[5, :] = 0.0
