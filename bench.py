@@ -474,6 +474,15 @@ def run_ours(args):
     t_leaf_cta = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), 3, 1)
     t_win_race = timed(lambda i: R.symm_spmv_exec(s_cf, R.RACE_EXEC_WINDOW_RACE, xs[i % RING], bs[i % RING],
                                                   stream), 3, 1)
+    # every phase in one cooperative launch, grid barriers between phases
+    R.race_set_launch(s_cf, 0, R.RACE_EXEC_PERSIST_CTA, 1, 1, 0, 8)
+    t_persist_cta = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), 3, 1)
+    # the paper's model proper: a leaf per worker (a group of 8 lanes), plain updates of b
+    R.race_set_launch(s_cf, 0, R.RACE_EXEC_LEAF_GROUP, 8, 1, 0, 8)
+    t_leaf_group = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), 3, 1)
+    R.race_set_launch(s_cf, 0, R.RACE_EXEC_PERSIST_GROUP, 8, 1, 0, 8)
+    t_persist_group = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), 3, 1)
+    R.race_poll_status(s_cf, stream)  # raises if a grid barrier gave up
     s_cf.free()
     # ---- the paper's comparison methods, multicolouring (MC) and algebraic block
     # multicolouring (ABMC, blocks of 64 rows), under the same conflict-free executors --------
@@ -486,8 +495,12 @@ def run_ours(args):
             ic = sc.info()
             R.race_set_launch(sc, 0, R.RACE_EXEC_LEAF_CTA, 1, 1, 0, 8)
             t_c = timed(lambda i: R.symm_spmv(sc, xs[i % RING], bs[i % RING], stream), 3, 1)
+            R.race_set_launch(sc, 0, R.RACE_EXEC_PERSIST_CTA, 1, 1, 0, 8)
+            t_cp = timed(lambda i: R.symm_spmv(sc, xs[i % RING], bs[i % RING], stream), 3, 1)
+            R.race_poll_status(sc, stream)
             colourings[label] = {"colours": ic["n_phases"], "leaves": ic["n_leaves"], "eta": ic["eta"],
-                                 "leaf_cta_ms_per_step": t_c / 3 * 1e3, "build_seconds": bsec}
+                                 "leaf_cta_ms_per_step": t_c / 3 * 1e3, "persist_cta_ms_per_step": t_cp / 3 * 1e3,
+                                 "build_seconds": bsec}
             sc.free()
     # ---- the same two kernels on the input order (no RACE permutation) --------------------
     s_nat = R.race_build(m, cfg["n_workers"], natural_order=True, windows=False, stream=stream)
@@ -630,15 +643,20 @@ def run_ours(args):
                           "speedup_vs_full": t_nat_full / t_nat_symm,
                           "what": "the same launches on the input order (RACE_FLAG_NATURAL_ORDER: no permutation)"},
         "race_conflict_free": {"leaf_cta_ms_per_step": t_leaf_cta / 3 * 1e3,
+                               "persist_cta_ms_per_step": t_persist_cta / 3 * 1e3,
+                               "leaf_group8_ms_per_step": t_leaf_group / 3 * 1e3,
+                               "persist_group8_ms_per_step": t_persist_group / 3 * 1e3,
                                "window_race_ms_per_step": t_win_race / 3 * 1e3,
                                "schedule": {"n_workers": cf["n_workers"], "max_depth": cf["max_depth"],
                                             "one_level_stage0": bool(cf.get("one_level_stage0", False)),
                                             "n_phases": info_cf["n_phases"], "n_leaves": info_cf["n_leaves"],
                                             "eta": info_cf["eta"]},
                                "colourings": colourings,
-                               "what": "RACE_EXEC_LEAF_CTA and RACE_EXEC_WINDOW_RACE (phase by phase, no two concurrent "
-                                       "leaves share an entry of b; x and b in that schedule's order) on a fully "
-                                       "recursed schedule, 3 steps each; the same leaf executor on the in-house MC "
+                               "what": "RACE_EXEC_LEAF_CTA, _WINDOW_RACE, _LEAF_GROUP (8 lanes a leaf, plain "
+                                       "updates of b) and the one-launch _PERSIST_CTA / _PERSIST_GROUP (grid "
+                                       "barriers between phases) -- phase by phase, no two concurrent leaves share "
+                                       "an entry of b; x and b in that schedule's order -- on a fully recursed "
+                                       "schedule, 3 steps each; the leaf-per-block executors on the in-house MC "
                                        "and ABMC colourings (race_build_coloring)"},
         "speedup_vs_full": t_full / t_symm,
         "matrix_powers": mpk,

@@ -204,8 +204,9 @@ int race_upload(race_schedule *s, void *stream);
  * i.e. b = A_u x + A_u^T x - diag(A) x (Alg. "SymmSpMV"), with the
  * schedule's current executor (race_set_launch; RACE_EXEC_LEAF_GROUP after
  * race_build).  The leaf executors (RACE_EXEC_LEAF_GROUP, _LEAF_CTA,
- * _WINDOW_RACE) run the schedule phase by phase, so that no two concurrent
- * leaves write the same entry of b; the row-parallel executors (_ATOMIC,
+ * _WINDOW_RACE, _PERSIST_GROUP, _PERSIST_CTA) run the schedule phase by
+ * phase, so that no two concurrent leaves write the same entry of b; the
+ * row-parallel executors (_ATOMIC,
  * _ROWS_RED, _STREAM_RED, _PIPE_RED, _WINDOW_RED, _DF64_RED, _SELL_DF64,
  * _STAGED) run all rows at once on the schedule's permuted matrix and
  * resolve the concurrent writes to b by reductions at L2.  x, b: device
@@ -294,6 +295,21 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    and step (4, or 8 when >= 8).  Needs no
                                    preparation and no memory beyond the
                                    schedule's.                              */
+#define RACE_EXEC_PERSIST_GROUP 11 /* LEAF_GROUP's work (one leaf per group of
+                                   group_lanes lanes, rows in order, plain
+                                   loads and stores of b) with every phase
+                                   in one cooperative launch: the phases
+                                   are separated by a grid barrier inside
+                                   the kernel instead of kernel boundaries
+                                   (Sec. 4.4.3).  Every barrier wait is
+                                   bounded; one that gives up records
+                                   RACE_ERR_TIMEOUT (race_poll_status) and
+                                   the launch ends with b incomplete.
+                                   Calls on one schedule must not overlap
+                                   (they share the barrier words).          */
+#define RACE_EXEC_PERSIST_CTA 12 /* the same for LEAF_CTA's work (one leaf
+                                   per block, the leaf's rows in parallel,
+                                   updates inside a leaf as L2 reductions)  */
 
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {
@@ -389,6 +405,20 @@ int race_poll_status(race_schedule *s, void *stream);
  * Errors: RACE_ERR_INVALID (NULL, aliasing), _UNSUPPORTED (host-only
  * schedule), _CUDA.                                                        */
 int race_probe_wait_timeout(const race_schedule *s, const double *x_d, double *b_d, void *stream);
+
+/* race_probe_barrier_timeout — diagnostic of the one-launch executors'
+ * grid barriers, computes nothing usable: runs RACE_EXEC_PERSIST_CTA on
+ * x_d / b_d (device arrays of n doubles, not aliasing; b_d is left
+ * undefined) with every barrier expecting one block more than the launch
+ * has (a wrong worker count made on the host) and a limit of 4096 polls
+ * (about 16 ms), so the first barrier gives up in every block and the
+ * kernel ends.  The
+ * kernel records RACE_ERR_TIMEOUT in the schedule's status word:
+ * race_poll_status then returns it once and clears it.  The paper has no
+ * counterpart (failure detection of this library's own kernels).
+ * Errors: RACE_ERR_INVALID (NULL, aliasing), _UNSUPPORTED (host-only
+ * schedule, or a schedule of a single phase: no barrier), _CUDA.          */
+int race_probe_barrier_timeout(const race_schedule *s, const double *x_d, double *b_d, void *stream);
 
 /* symm_spmv_exec — symm_spmv with an explicit executor (RACE_EXEC_*).
  * Same arguments, layout and errors as symm_spmv.                          */

@@ -51,7 +51,7 @@ EXPORTED = ("race_default_params", "race_build", "symm_spmv", "symm_spmv_exec", 
             "race_features", "race_mlp_param_count", "race_mlp_act_size", "race_mlp_work_size", "race_mlp_forward",
             "race_mlp_backward", "race_mlp_adam", "race_upload", "race_import", "symm_gs", "symm_kacz",
             "race_probe_wait_timeout", "race_probe_peaks", "race_matrix_powers", "race_probe_reductions",
-            "race_build_coloring")
+            "race_build_coloring", "race_probe_barrier_timeout")
 
 RACE_EXEC_LEAF_GROUP = 0
 RACE_EXEC_LEAF_CTA = 1
@@ -64,6 +64,8 @@ RACE_EXEC_WINDOW_RACE = 7
 RACE_EXEC_DF64_RED = 8
 RACE_EXEC_SELL_DF64 = 9
 RACE_EXEC_STAGED = 10
+RACE_EXEC_PERSIST_GROUP = 11
+RACE_EXEC_PERSIST_CTA = 12
 
 
 class race_launch(ctypes.Structure):
@@ -155,6 +157,8 @@ def lib():
     L.race_probe_peaks.restype = ctypes.c_int
     L.race_probe_wait_timeout.argtypes = [vp, vp, vp, vp]
     L.race_probe_wait_timeout.restype = ctypes.c_int
+    L.race_probe_barrier_timeout.argtypes = [vp, vp, vp, vp]
+    L.race_probe_barrier_timeout.restype = ctypes.c_int
     L.symm_spmv_noalloc.argtypes = [i32, ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     L.symm_spmv_noalloc.restype = ctypes.c_int
     pvp = ctypes.POINTER(vp)
@@ -419,6 +423,14 @@ def race_probe_wait_timeout(s: Schedule, x, b, stream=None):
     """Diagnostic: run the staged kernel with waits that give up (b undefined);
     the next race_poll_status then raises RACE_ERR_TIMEOUT once."""
     _check(lib().race_probe_wait_timeout(s.handle, _ptr(x), _ptr(b), _stream(stream)), "race_probe_wait_timeout")
+
+
+def race_probe_barrier_timeout(s: Schedule, x, b, stream=None):
+    """Diagnostic: run the one-launch executor with barriers that expect one
+    block too many (b undefined); the next race_poll_status then raises
+    RACE_ERR_TIMEOUT once."""
+    _check(lib().race_probe_barrier_timeout(s.handle, _ptr(x), _ptr(b), _stream(stream)),
+           "race_probe_barrier_timeout")
 
 
 class Batch:

@@ -47,6 +47,7 @@
 #include "df64.cuh"
 #include "fp64_share.cuh"
 #include "race_internal.h"
+#include "red.cuh"
 
 namespace race_mpk {
 
@@ -99,16 +100,16 @@ __device__ __forceinline__ void warp_rows(int32_t row, bool live, const int32_t*
             acc = fma(a[u], xc[u], acc);
             if (c[u] == row || !scatter) continue;
             if (use64) {
-                atomicAdd(dst + c[u], a[u] * xr);
+                red_add_f64(dst + c[u], a[u] * xr);
             } else if (!df64::is_zero(a[u])) {
                 float ah, al, ph, pl;
                 df64::split_in_range(a[u], ah, al);
                 df64::mul(ah, al, xrh, xrl, ph, pl);
-                atomicAdd(dst + c[u], df64::join(ph, pl));
+                red_add_f64(dst + c[u], df64::join(ph, pl));
             }
         }
     }
-    if (live) atomicAdd(dst + row, acc);
+    if (live) red_add_f64(dst + row, acc);
 }
 
 template <int B>

@@ -29,10 +29,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 void release_device(race_schedule* s) {
     void* ptrs[] = {s->d_rp, s->d_col, s->d_val, s->d_leaf_lo, s->d_leaf_hi, s->d_perm,
                     s->d_frp, s->d_fcol, s->d_fval, s->d_blk, s->d_fblk, s->d_status,
-                    s->mpk.d_reach, s->mpk.d_flags};
+                    s->mpk.d_reach, s->mpk.d_flags, s->d_stage, s->d_bar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     s->mpk = MpkState();
+    s->d_stage = nullptr;
+    s->d_bar = nullptr;
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
@@ -219,6 +221,12 @@ static int upload_schedule(race_schedule* s, cudaStream_t st) {
     if (rc == RACE_OK) {
         std::vector<int32_t> z(1, 0);
         rc = upload(z, &s->d_status, st);
+    }
+    if (rc == RACE_OK) rc = upload(s->plan.stage_ptr, &s->d_stage, st);
+    if (rc == RACE_OK) {
+        // barrier words, a leaf ticket per phase, block-ranking counters
+        std::vector<uint32_t> z(race_persist_bar_words(s->plan.stage_ptr.size()), 0u);
+        rc = upload(z, &s->d_bar, st);
     }
     if (rc == RACE_OK && s->max_row_upper + 1 <= kWindowCap && s->want_windows) {
         // window executors: flat tiles over all rows, and tiles of every

@@ -153,6 +153,8 @@ struct race_schedule {
     int32_t* d_fblk = nullptr;  // row-block starts of the full CRS
     int64_t n_fblk = 0;
     int32_t* d_status = nullptr;  // device status word (RACE_ERR_TIMEOUT)
+    int32_t* d_stage = nullptr;   // plan.stage_ptr on the device (one-launch executors)
+    uint32_t* d_bar = nullptr;    // one-launch executors: barrier words, leaf tickets, block ranking
     int32_t max_row_upper = 0, max_row_full = 0;
     WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
     // double-float executor: off-diagonal values range-checked on first use
@@ -203,6 +205,12 @@ int race_sell_launch(const race_schedule* s, const double* x, double* b, cudaStr
 constexpr uint32_t kStagedSpinLimit = 1u << 26;
 int race_staged_launch(const race_schedule* s, const race_launch& l, const double* x, double* b, cudaStream_t st,
                        uint32_t spin_limit, uint32_t extra_tx);
+
+// One-launch executors (persist_kernels.cu): every phase in one cooperative
+// launch with bounded grid barriers between phases.
+int race_persist_launch(const race_schedule* s, int32_t executor, const double* x, double* b, cudaStream_t st);
+// Words of s->d_bar for a schedule of stage_ptr_size - 1 phases.
+size_t race_persist_bar_words(size_t stage_ptr_size);
 
 // Multiprocessor count of the current device (cached per device).
 int race_device_sms();

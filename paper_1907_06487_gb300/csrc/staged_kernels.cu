@@ -51,6 +51,7 @@
 #include "df64.cuh"
 #include "race_internal.h"
 #include "stream_engine.cuh"
+#include "red.cuh"
 
 namespace race_stg {
 
@@ -177,14 +178,14 @@ __device__ __forceinline__ void tile_rows(int32_t row, bool live, int32_t lo, in
             }
             if (c[u] != row && scatter) {
                 if constexpr (TP64) {
-                    atomicAdd(b + c[u], df64::widen(a[u]) * xr);
+                    red_add_f64(b + c[u], df64::widen(a[u]) * xr);
                 } else {
                     if (abad | xr_bad) {
                         defer = true;
                     } else if (!df64::is_zero(a[u])) {
                         float ph, pl;
                         df64::mul(ah, al, xrh, xrl, ph, pl);
-                        atomicAdd(b + c[u], df64::join(ph, pl));
+                        red_add_f64(b + c[u], df64::join(ph, pl));
                     }
                 }
             }
@@ -204,7 +205,7 @@ __device__ __forceinline__ void tile_rows(int32_t row, bool live, int32_t lo, in
                 if (!rs_df || abad || df64::split(xv, xh, xl)) acc = fma(df64::widen(av), xv, acc);
             }
             if constexpr (!TP64) {
-                if (cj != row && scatter && (abad || xr_bad)) atomicAdd(b + cj, df64::widen(av) * xr);
+                if (cj != row && scatter && (abad || xr_bad)) red_add_f64(b + cj, df64::widen(av) * xr);
             }
         }
     }
@@ -218,7 +219,7 @@ __device__ __forceinline__ void tile_rows(int32_t row, bool live, int32_t lo, in
         }
         total = any_defer ? acc + v : v;
     }
-    if (live) atomicAdd(b + row, total);
+    if (live) red_add_f64(b + row, total);
 }
 
 template <typename VT, int B, int NS, bool RS64, bool TP64>

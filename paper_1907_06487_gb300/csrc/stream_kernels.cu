@@ -20,6 +20,7 @@
 
 #include "race_internal.h"
 #include "stream_engine.cuh"
+#include "red.cuh"
 
 namespace race_dev {
 
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_stream(int64_t nblk, const int32_t
                         prod[j] = a * xv[u];  // diagonal: x[col] is x[row]
                     } else {
                         prod[j] = a * xv[u];
-                        atomicAdd(b + cj[u], a * __ldg(x + row));
+                        red_add_f64(b + cj[u], a * __ldg(x + row));
                     }
                 }
             }
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_stream(int64_t nblk, const int32_t
             double sum = 0.0;
             for (int j = a; j < z; ++j) sum += prod[j];
             if (MODE == kFull) b[g.r0 + r] = sum;
-            else atomicAdd(b + g.r0 + r, sum);
+            else red_add_f64(b + g.r0 + r, sum);
         }
         __syncthreads();
         if (tid == 0) {
@@ -328,9 +329,9 @@ __global__ void k_tail(int32_t n, const int32_t* __restrict__ rp, const int32_t*
             const int32_t c = __ldg(col + j);
             const double a = __ldg(val + j);
             acc += a * __ldg(x + c);
-            if (c != r) atomicAdd(b + c, a * xr);
+            if (c != r) red_add_f64(b + c, a * xr);
         }
-        atomicAdd(b + r, acc);
+        red_add_f64(b + r, acc);
     }
 }
 
