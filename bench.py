@@ -521,24 +521,25 @@ def run_ours(args):
     s32.free()
     # ---- end to end through host buffers: H2D x, permute, SymmSpMV, unpermute, D2H b --------
     # Each step copies its x in and its b out; copies run on their own streams
-    # (double-buffered), so step i's read-back overlaps step i+1's upload and
+    # over two buffer sets, so step i's read-back overlaps step i+1's upload and
     # compute, as a caller streaming vectors through the library would run it.
     s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    xh = [torch.from_numpy(x_host).pin_memory() for _ in range(2)]
-    bh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
-    xd = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
-    bd = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+    NB = 2  # buffer sets in flight (three measured slower: 0.72 against 0.51-0.53 ms per step)
+    xh = [torch.from_numpy(x_host).pin_memory() for _ in range(NB)]
+    bh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(NB)]
+    xd = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(NB)]
+    bd = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(NB)]
     xpd, bpd = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2))
-    ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+    ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(NB)] for _ in range(3))
 
     def e2e_step(i):
-        j = i % 2
-        s_in.wait_event(ev_c[j])        # xd[j] consumed by the step two back
+        j = i % NB
+        s_in.wait_event(ev_c[j])        # xd[j] consumed by the step NB back
         with torch.cuda.stream(s_in):
             xd[j].copy_(xh[j], non_blocking=True)
         ev_in[j].record(s_in)
         stream.wait_event(ev_in[j])
-        stream.wait_event(ev_out[j])    # bd[j] read back by the step two back
+        stream.wait_event(ev_out[j])    # bd[j] read back by the step NB back
         R.race_permute(s, xd[j], xpd, 1, stream)
         R.symm_spmv(s, xpd, bpd, stream)
         R.race_unpermute(s, bpd, bd[j], 1, stream)
@@ -566,13 +567,40 @@ def run_ours(args):
         return e0.elapsed_time(e1) * 1e-3
 
     t_e2e = timed_e2e(args.steps, args.warmup)
+
+    # the copies alone, both directions at once on their own streams: the floor
+    # the host link sets for the end-to-end step
+    def timed_copies(steps, warmup):
+        def one(i):
+            j = i % NB
+            with torch.cuda.stream(s_in):
+                xd[j].copy_(xh[j], non_blocking=True)
+            with torch.cuda.stream(s_out):
+                bh[j].copy_(bd[j], non_blocking=True)
+        for i in range(warmup):
+            one(i)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
+        for i in range(steps):
+            one(i)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) * 1e-3
+
+    t_copies = timed_copies(args.steps, args.warmup)
     # the read-back must equal the device-timed result for the same x (xs[0] is x_host permuted)
     with torch.cuda.stream(stream):
         R.symm_spmv(s, xs[0], bs[0], stream)
         R.race_unpermute(s, bs[0], bd[0], 1, stream)
     stream.synchronize()
     ref = bd[0].cpu().numpy()
-    got = bh[(args.steps - 1) % 2].numpy()
+    got = bh[(args.steps - 1) % NB].numpy()
     e2e_ok = bool(np.allclose(got, ref, rtol=1e-12, atol=1e-12 * float(np.abs(ref).max())))
     t_symm, t_full, t_e2e, t_red, t_col, t_strict = max_over_ranks([t_symm, t_full, t_e2e, t_red, t_col, t_strict],
                                                                    world, dev)
@@ -664,8 +692,12 @@ def run_ours(args):
         "spmm_headline": spmm_head,
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                 "ms_per_step": t_e2e / args.steps * 1e3, "matches_device_result": e2e_ok,
+                "copies_only_ms_per_step": t_copies / args.steps * 1e3,
+                "host_link_gbs": 16 * n / (t_copies / args.steps) / 1e9,
+                "frac_of_copy_floor": t_copies / t_e2e,
                 "how": "per step: pinned H2D of x, permute, SymmSpMV, unpermute, D2H of b into pinned memory; "
-                       "copies on their own streams, double-buffered across steps"},
+                       "copies on their own streams, double-buffered across steps; copies_only: the same two "
+                       "copies per step with no compute (the host link's floor for the step)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,

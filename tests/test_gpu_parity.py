@@ -183,8 +183,9 @@ def test_full_size_xxz26(dev, oracle_mod):
     lc = cfg["launch"]
     R.race_set_launch(s, 0, **lc)
     assert_parity(run_symm(s, m, x, dev)[rows], bref, sc)
-    for ex in (cfg["executor"], 0):
+    for ex in (cfg["executor"], 0, R.RACE_EXEC_PERSIST_CTA, R.RACE_EXEC_PERSIST_GROUP):
         b = run_symm(s, m, x, dev, ex)
+        R.race_poll_status(s)  # no grid barrier gave up
         assert_parity(b[rows], bref, sc)
     # property at every row: the uniform vector is an eigenvector, eigenvalue L/4 = 6.5,
     # and every partial sum is a multiple of 1/4 (exact in FP64, and in the
@@ -193,6 +194,7 @@ def test_full_size_xxz26(dev, oracle_mod):
     assert np.all(run_symm(s, m, ones, dev) == 6.5)
     b1 = run_symm(s, m, ones, dev, cfg["executor"])
     assert np.all(b1 == 6.5)
+    assert np.all(run_symm(s, m, ones, dev, R.RACE_EXEC_PERSIST_CTA) == 6.5)
 
 
 _ST27 = {}
