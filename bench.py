@@ -437,6 +437,9 @@ def run_ours(args):
     R.race_set_launch(s, 0, executor=R.RACE_EXEC_ROWS_RED, group_lanes=1, rows_per_group=1, blocks_per_sm=0,
                       regs_per_row=8, fp64_quarters=4)
     t_strict = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
+    # ---- the same arithmetic and shape, phase by phase on the same schedule -----------------
+    R.race_set_launch(s, 0, **dict(lc, executor=R.RACE_EXEC_PHASE_DF64))
+    t_phased = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     R.race_set_launch(s, 0, **lc)
     # ---- the limit the reduction-based executors share: the scatter's reductions at L2 ------
     def probe(mode):
@@ -602,8 +605,8 @@ def run_ours(args):
     ref = bd[0].cpu().numpy()
     got = bh[(args.steps - 1) % NB].numpy()
     e2e_ok = bool(np.allclose(got, ref, rtol=1e-12, atol=1e-12 * float(np.abs(ref).max())))
-    t_symm, t_full, t_e2e, t_red, t_col, t_strict = max_over_ranks([t_symm, t_full, t_e2e, t_red, t_col, t_strict],
-                                                                   world, dev)
+    t_symm, t_full, t_e2e, t_red, t_col, t_strict, t_phased = max_over_ranks(
+        [t_symm, t_full, t_e2e, t_red, t_col, t_strict, t_phased], world, dev)
     s.free()
     del xs, bs, xd, bd, xpd, bpd
     torch.cuda.empty_cache()
@@ -613,7 +616,8 @@ def run_ours(args):
     value = whole_job_rate(world, flops, args.steps, t_symm) / 1e9
     full_gflops = whole_job_rate(world, flops, args.steps, t_full) / 1e9
     e2e_value = whole_job_rate(world, flops, args.steps, t_e2e) / 1e9
-    launches_per_step = 1 if lc["executor"] >= R.RACE_EXEC_ATOMIC else info["n_phases"]
+    per_phase = (R.RACE_EXEC_LEAF_GROUP, R.RACE_EXEC_LEAF_CTA, R.RACE_EXEC_WINDOW_RACE, R.RACE_EXEC_PHASE_DF64)
+    launches_per_step = info["n_phases"] if lc["executor"] in per_phase else 1
 
     # ---- the other workloads of the default run (rank 0's replica measures them too) --------
     extra = {}
@@ -650,6 +654,13 @@ def run_ours(args):
                         "gflops": flops / (t_strict / args.steps) / 1e9,
                         "frac": sym_bytes / (t_strict / args.steps) / 1e9 / peak,
                         "launch": "RACE_EXEC_ROWS_RED, one row per lane, all arithmetic FP64 (the plain FP64 form)"},
+        "race_phased": {"ms_per_step": t_phased / args.steps * 1e3,
+                        "gflops": flops / (t_phased / args.steps) / 1e9,
+                        "frac": sym_bytes / (t_phased / args.steps) / 1e9 / peak,
+                        "vs_headline": t_phased / t_symm, "n_phases": info["n_phases"], "n_leaves": info["n_leaves"],
+                        "what": "RACE_EXEC_PHASE_DF64: the headline's arithmetic and launch shape run phase by phase "
+                                "(one launch per phase over its leaves' rows, no two concurrent leaves sharing an "
+                                "entry of b; updates inside a leaf are L2 reductions) on the same schedule"},
         "reduction_floor": {"ms_per_step": t_red / args.steps * 1e3, "columns_only_ms_per_step": t_col / args.steps * 1e3,
                             "frac": (t_red / args.steps) / per_step,
                             "what": "race_probe_scatter on the same schedule: the transposed update's L2 reductions "
@@ -754,6 +765,8 @@ def stencil_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, cei
     R.race_set_launch(s, 0, executor=R.RACE_EXEC_ROWS_RED, group_lanes=1, rows_per_group=1, blocks_per_sm=0,
                       regs_per_row=8, fp64_quarters=4)
     t_strict = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), K, W) / K
+    R.race_set_launch(s, 0, **dict(lc, executor=R.RACE_EXEC_PHASE_DF64))
+    t_phased = timed(lambda i: R.symm_spmv(s, xs[i % RING], bs[i % RING], stream), K, W) / K
     R.race_set_launch(s, 0, **lc)
     t_f32 = timed(lambda i: R.symm_spmv(s32, xs[i % RING], bs[i % RING], stream), K, W) / K
     with torch.cuda.stream(stream):
@@ -777,6 +790,9 @@ def stencil_block(args, R, configs, pm, dev, stream, timed, peak, peak_kind, cei
                                                  ceil["load_only_gbs"], None, pm.symm_bytes(n, nu))},
         "strict_fp64": {"ms_per_step": t_strict * 1e3, "gflops": flops / t_strict / 1e9,
                         "frac": pm.symm_bytes_rmw(n, nu) / t_strict / 1e9 / hbm},
+        "race_phased": {"ms_per_step": t_phased * 1e3, "gflops": flops / t_phased / 1e9,
+                        "frac": pm.symm_bytes_rmw(n, nu) / t_phased / 1e9 / hbm, "vs_headline": t_phased / t_symm,
+                        "n_phases": info["n_phases"], "n_leaves": info["n_leaves"]},
         "fp32_values": {"ms_per_step": t_f32 * 1e3, "gflops": flops / t_f32 / 1e9,
                         "frac": pm.symm_bytes_rmw(n, nu, 1, 4) / t_f32 / 1e9 / hbm},
         "spmv_full": {"ms_per_step": t_full * 1e3, "gflops": flops / t_full / 1e9,

@@ -204,13 +204,13 @@ int race_upload(race_schedule *s, void *stream);
  * i.e. b = A_u x + A_u^T x - diag(A) x (Alg. "SymmSpMV"), with the
  * schedule's current executor (race_set_launch; RACE_EXEC_LEAF_GROUP after
  * race_build).  The leaf executors (RACE_EXEC_LEAF_GROUP, _LEAF_CTA,
- * _WINDOW_RACE, _PERSIST_GROUP, _PERSIST_CTA) run the schedule phase by
- * phase, so that no two concurrent leaves write the same entry of b; the
- * row-parallel executors (_ATOMIC,
- * _ROWS_RED, _STREAM_RED, _PIPE_RED, _WINDOW_RED, _DF64_RED, _SELL_DF64,
- * _STAGED) run all rows at once on the schedule's permuted matrix and
- * resolve the concurrent writes to b by reductions at L2.  x, b: device
- * arrays of n doubles in permuted order.                                  */
+ * _WINDOW_RACE, _PERSIST_GROUP, _PERSIST_CTA, _PHASE_DF64) run the schedule
+ * phase by phase, so that no two concurrent leaves write the same entry of
+ * b; the row-parallel executors (_ATOMIC, _ROWS_RED, _STREAM_RED,
+ * _PIPE_RED, _WINDOW_RED, _DF64_RED, _SELL_DF64, _STAGED) run all rows at
+ * once on the schedule's permuted matrix and resolve the concurrent writes
+ * to b by reductions at L2.  x, b: device arrays of n doubles in permuted
+ * order.                                                                   */
 int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stream);
 
 /* Executors of SymmSpMV (symm_spmv_exec).                                  */
@@ -310,6 +310,21 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
 #define RACE_EXEC_PERSIST_CTA 12 /* the same for LEAF_CTA's work (one leaf
                                    per block, the leaf's rows in parallel,
                                    updates inside a leaf as L2 reductions)  */
+#define RACE_EXEC_PHASE_DF64 13 /* DF64_RED's arithmetic (one row per lane,
+                                   FP64 row sums, fp64_quarters of the row
+                                   groups' transposed products in FP64, the
+                                   rest double-float) phase by phase: one
+                                   launch per phase over the rows of the
+                                   phase's leaves, cut into chunks of at most
+                                   256 rows of one leaf, a block per chunk at
+                                   a time.  No two concurrently running
+                                   leaves share an entry of b; the rows of
+                                   one leaf may run in different blocks, so
+                                   updates inside a leaf are L2 reductions.
+                                   blocks_per_sm, regs_per_row (4 or 8) as
+                                   for DF64_RED; SymmSpMM runs DF64_RED's
+                                   row-parallel kernel.  Same range check
+                                   and error bound as DF64_RED.             */
 
 /* Launch shape of a kernel family; set by an autotuner or by hand.          */
 typedef struct {

@@ -66,6 +66,7 @@ RACE_EXEC_SELL_DF64 = 9
 RACE_EXEC_STAGED = 10
 RACE_EXEC_PERSIST_GROUP = 11
 RACE_EXEC_PERSIST_CTA = 12
+RACE_EXEC_PHASE_DF64 = 13
 
 
 class race_launch(ctypes.Structure):

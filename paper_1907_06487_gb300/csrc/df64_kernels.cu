@@ -98,9 +98,29 @@ __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, 
     return acc;
 }
 
-// G lanes per row, rows strided over the grid; the lanes' FP64 row sums are
-// combined by shuffles and go to b[row] as a reduction at L2 (b is zeroed
-// first; transposed updates of other rows land there too).
+// One row on its G lanes: the FP64 row sum (combined by shuffles) goes to
+// b[row] as a reduction at L2, the transposed updates of the other rows land
+// there too (b is zeroed first).  warp64: this row's transposed products in
+// FP64 (warp-uniform).
+template <typename VT, int G, int B>
+__device__ __forceinline__ void row_df64(int32_t row, int lane, unsigned mask, bool warp64,
+                                         const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                         const VT* __restrict__ val, const double* __restrict__ x, double* b) {
+    const int32_t lo = __ldg(rp + row), hi = __ldg(rp + row + 1);
+    const double xr = __ldg(x + row);
+    float xrh, xrl;
+    const int st = df64::split(xr, xrh, xrl);
+    double acc;
+    if (st != 0) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+    else if (xrh == 0.0f) acc = lane_row<VT, G, kNone, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+    else if (warp64) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+    else acc = lane_row<VT, G, kSplit, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
+    if (lane == 0) atomicAdd(b + row, acc);
+}
+
+// G lanes per row, rows strided over the grid.
 template <typename VT, int G, int B>
 __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const VT* __restrict__ val,
@@ -113,20 +133,31 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
     const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
     for (int64_t r = gid; r < n; r += ngroups) {
-        const int32_t row = static_cast<int32_t>(r);
         const bool warp64 = fp64_group(static_cast<uint32_t>(static_cast<uint64_t>(r) / (32 / G)), fp64_quarters);
-        const int32_t lo = __ldg(rp + row), hi = __ldg(rp + row + 1);
-        const double xr = __ldg(x + row);
-        float xrh, xrl;
-        const int st = df64::split(xr, xrh, xrl);
-        double acc;
-        if (st != 0) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-        else if (xrh == 0.0f) acc = lane_row<VT, G, kNone, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-        else if (warp64) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-        else acc = lane_row<VT, G, kSplit, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
-        if (lane == 0) atomicAdd(b + row, acc);
+        row_df64<VT, G, B>(static_cast<int32_t>(r), lane, mask, warp64, rp, col, val, x, b);
+    }
+}
+
+// One phase of the schedule (executor RACE_EXEC_PHASE_DF64): the rows of the
+// phase's leaves, cut into chunks of at most kBlock consecutive rows of one
+// leaf (chunks[q] = {first row, row count}); a block takes a chunk, one row
+// per thread, and the blocks take the chunks in turn.  The rows of one leaf
+// may run in different blocks, so their updates of shared entries of b are
+// L2 reductions; the leaves of a phase never share an entry of b (Sec. 4.2),
+// and the phases run in order, one launch each.
+template <typename VT, int B>
+__global__ void __launch_bounds__(kBlock) k_symm_df64_phase(const int2* __restrict__ chunks, int32_t nchunks,
+                                                           const int32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ col,
+                                                           const VT* __restrict__ val, const double* __restrict__ x,
+                                                           double* b, int fp64_quarters, uint32_t chunk_base) {
+    for (int32_t q = blockIdx.x; q < nchunks; q += gridDim.x) {
+        const int2 ch = __ldg(chunks + q);
+        const bool warp64 = fp64_group((chunk_base + static_cast<uint32_t>(q)) * (kBlock / 32) + (threadIdx.x >> 5),
+                                       fp64_quarters);
+        if (static_cast<int32_t>(threadIdx.x) < ch.y)
+            row_df64<VT, 1, B>(ch.x + static_cast<int32_t>(threadIdx.x), 0, 1u << (threadIdx.x & 31), warp64, rp,
+                               col, val, x, b);
     }
 }
 
@@ -182,6 +213,39 @@ int race_df64_prepare(const race_schedule* s) {
     if (st == -1) {
         race_set_detail("an off-diagonal value outside the double-float magnitude range [2^-50, 2^51)");
         return RACE_ERR_UNSUPPORTED;
+    }
+    return RACE_OK;
+}
+
+int race_df64_phase_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st) {
+    int rc = race_df64_prepare(s);
+    if (rc) return rc;
+    const bool mine = s->launch.executor == RACE_EXEC_PHASE_DF64;
+    const int64_t per_sm = mine && s->launch.blocks_per_sm > 0 ? s->launch.blocks_per_sm : (2048 / kBlock);
+    const int64_t cap = static_cast<int64_t>(sm_count_of_device()) * per_sm;
+    const int q64 = mine ? s->launch.fp64_quarters : 0;
+    const bool b8 = mine && s->launch.regs_per_row >= 8;
+    const auto& cp = s->chunk_ptr;
+    for (size_t p = 0; p + 1 < cp.size(); ++p) {
+        const int64_t nch = cp[p + 1] - cp[p];
+        if (nch == 0) continue;
+        const int grid = static_cast<int>(std::min(nch, cap));
+        const int2* ch = s->d_chunks + cp[p];
+        const uint32_t base = static_cast<uint32_t>(cp[p]);
+        if (s->val_type == RACE_F64) {
+            const double* v = static_cast<const double*>(s->d_val);
+            if (b8) k_symm_df64_phase<double, 8><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
+            else k_symm_df64_phase<double, 4><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
+        } else {
+            const float* v = static_cast<const float*>(s->d_val);
+            if (b8) k_symm_df64_phase<float, 8><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
+            else k_symm_df64_phase<float, 4><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
+        }
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        race_set_detail(std::string("k_symm_df64_phase: ") + cudaGetErrorString(e));
+        return RACE_ERR_CUDA;
     }
     return RACE_OK;
 }

@@ -785,7 +785,8 @@ int launch_mm_k(const race_schedule* s, int32_t k, const double* X, double* B, c
         const int32_t n = s->plan.n;
         const int R = s->launch.rows_per_group >= 4 ? 4 : (s->launch.rows_per_group >= 2 ? 2 : 1);
         const VT* v = static_cast<const VT*>(s->d_val);
-        const bool df = s->launch.executor == RACE_EXEC_DF64_RED || s->launch.executor == RACE_EXEC_SELL_DF64;
+        const bool df = s->launch.executor == RACE_EXEC_DF64_RED || s->launch.executor == RACE_EXEC_SELL_DF64 ||
+                        s->launch.executor == RACE_EXEC_PHASE_DF64;
         const int q64 = df ? s->launch.fp64_quarters : 0;
         if (df) {
             const int rc = race_df64_prepare(s);
@@ -878,6 +879,7 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
     if (s->launch.executor == RACE_EXEC_STAGED) return race_staged_launch(s, s->launch, x_d, b_d, st, kStagedSpinLimit, 0);
     if (s->launch.executor == RACE_EXEC_PERSIST_GROUP || s->launch.executor == RACE_EXEC_PERSIST_CTA)
         return race_persist_launch(s, s->launch.executor, x_d, b_d, st);
+    if (s->launch.executor == RACE_EXEC_PHASE_DF64) return race_df64_phase_launch(s, x_d, b_d, st);
     rc = s->val_type == RACE_F64 ? launch_symm_exec<double>(s, s->launch.executor, x_d, b_d, st)
                                  : launch_symm_exec<float>(s, s->launch.executor, x_d, b_d, st);
     if (rc) return rc;
@@ -887,7 +889,7 @@ int symm_spmv(const race_schedule* s, const double* x_d, double* b_d, void* stre
 int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, double* b_d, void* stream) {
     int rc = precheck(s, x_d, b_d);
     if (rc) return rc;
-    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_PERSIST_CTA) {
+    if (executor < RACE_EXEC_LEAF_GROUP || executor > RACE_EXEC_PHASE_DF64) {
         race_set_detail("unknown executor");
         return RACE_ERR_INVALID;
     }
@@ -902,6 +904,7 @@ int symm_spmv_exec(const race_schedule* s, int32_t executor, const double* x_d, 
     if (executor == RACE_EXEC_STAGED) return race_staged_launch(s, s->launch, x_d, b_d, st, kStagedSpinLimit, 0);
     if (executor == RACE_EXEC_PERSIST_GROUP || executor == RACE_EXEC_PERSIST_CTA)
         return race_persist_launch(s, executor, x_d, b_d, st);
+    if (executor == RACE_EXEC_PHASE_DF64) return race_df64_phase_launch(s, x_d, b_d, st);
     rc = s->val_type == RACE_F64 ? launch_symm_exec<double>(s, executor, x_d, b_d, st)
                                  : launch_symm_exec<float>(s, executor, x_d, b_d, st);
     if (rc) return rc;
@@ -956,18 +959,19 @@ int race_set_launch(race_schedule* s, int32_t which, const race_launch* l) {
     const bool g_ok = l->group_lanes == 1 || l->group_lanes == 2 || l->group_lanes == 4 || l->group_lanes == 8 || l->group_lanes == 16 || l->group_lanes == 32;
     const bool u_ok = l->rows_per_group == 1 || l->rows_per_group == 2 || l->rows_per_group == 4 || l->rows_per_group == 8;
     if (!g_ok || !u_ok || l->blocks_per_sm < 0 || l->blocks_per_sm > 2048 / kBlock ||
-        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_PERSIST_CTA || l->regs_per_row < 0 ||
+        l->executor < RACE_EXEC_LEAF_GROUP || l->executor > RACE_EXEC_PHASE_DF64 || l->regs_per_row < 0 ||
         l->regs_per_row > 16 || l->fp64_quarters < 0 || l->fp64_quarters > 4 || l->rowsum_fp64_quarters < 0 ||
         l->rowsum_fp64_quarters > 4 || (which != 0 && which != 1)) {
         race_set_detail("launch configuration out of range");
         return RACE_ERR_INVALID;
     }
-    if (which == 0 && (l->executor == RACE_EXEC_DF64_RED || l->executor == RACE_EXEC_SELL_DF64)) {
+    if (which == 0 && (l->executor == RACE_EXEC_DF64_RED || l->executor == RACE_EXEC_SELL_DF64 ||
+                       l->executor == RACE_EXEC_PHASE_DF64)) {
         if (s->host_only) {
             race_set_detail("schedule was built with RACE_FLAG_HOST_ONLY");
             return RACE_ERR_UNSUPPORTED;
         }
-        const int rc = l->executor == RACE_EXEC_DF64_RED ? race_df64_prepare(s) : race_sell_prepare(s);
+        const int rc = l->executor == RACE_EXEC_SELL_DF64 ? race_sell_prepare(s) : race_df64_prepare(s);
         if (rc) return rc;
     }
     if (which == 0) {

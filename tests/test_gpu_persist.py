@@ -1,6 +1,8 @@
 """GPU parity of the one-launch RACE executors (RACE_EXEC_PERSIST_GROUP: one
 leaf per lane group, plain updates of b; RACE_EXEC_PERSIST_CTA: one leaf per
-block) against the CPU oracle, under the FP64 bound
+block) and of the phase-by-phase double-float executor
+(RACE_EXEC_PHASE_DF64: one launch per phase over the leaves' rows in chunks)
+against the CPU oracle, under the FP64 bound
 |b_i - b_ref_i| <= 1e-12 sum_j |a_ij||x_j|.
 
 Cases: fully recursed RACE schedules (many phases, the grid barrier between
@@ -161,3 +163,56 @@ def test_barrier_timeout_is_reported(dev, oracle_mod, matgen_mod):
     with pytest.raises(R.RaceError) as ei:
         R.race_probe_barrier_timeout(one, xd[:1], bd[:1])
     assert ei.value.code == R.RACE_ERR_UNSUPPORTED
+
+
+PD = R.RACE_EXEC_PHASE_DF64
+
+
+@pytest.mark.parametrize("per_step,quarters", [(4, 2), (8, 1), (4, 0), (4, 4)])
+@pytest.mark.parametrize("which", sorted(MATS))
+def test_phase_df64(dev, oracle_mod, matgen_mod, which, per_step, quarters):
+    # the double-float arithmetic phase by phase, the leaves' rows in chunks
+    # of at most 256 rows: deep schedules (many phases, leaves of a few rows)
+    # and depth-1 ones (few phases, leaves of thousands of rows)
+    m = MATS[which](matgen_mod)
+    x = matgen_mod.uniform(m["n"], 23, -1.0, 1.0)
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
+    for depth in (-1, 1):
+        s = R.race_build(m, 96, max_depth=depth, rcm=(which == "geometric"))
+        R.race_set_launch(s, 0, executor=PD, group_lanes=1, rows_per_group=1, blocks_per_sm=0,
+                          regs_per_row=per_step, fp64_quarters=quarters)
+        check(run(s, x, dev), bref, sc)
+        # by symm_spmv_exec while the schedule's launch names another executor
+        R.race_set_launch(s, 0, executor=R.RACE_EXEC_ROWS_RED, group_lanes=2, rows_per_group=1, blocks_per_sm=0,
+                          regs_per_row=8)
+        perm = s.perm()
+        xd = torch.from_numpy(np.ascontiguousarray(x[perm])).to(dev)
+        bd = torch.full_like(xd, np.nan)
+        R.symm_spmv_exec(s, PD, xd, bd)
+        torch.cuda.synchronize()
+        b = np.empty_like(x)
+        b[perm] = bd.cpu().numpy()
+        check(b, bref, sc)
+
+
+def test_phase_df64_fp32_colourings_degenerate(dev, oracle_mod, matgen_mod):
+    m = matgen_mod.stencil3d(13, npt=27, seed=9)
+    m32 = dict(m, val=m["val"].astype(np.float32).astype(np.float64))
+    x = matgen_mod.uniform(m["n"], 24, -1.0, 1.0)
+    s = R.race_build(m, 64, max_depth=-1, val_type=R.RACE_F32)
+    R.race_set_launch(s, 0, executor=PD, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4,
+                      fp64_quarters=2)
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m32), x)
+    check(run(s, x, dev), bref, sc)
+    bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(m), x)
+    for method, bs in ((R.RACE_COLOR_MC, 1), (R.RACE_COLOR_ABMC, 32)):
+        c = R.race_build_coloring(m, method, bs)
+        R.race_set_launch(c, 0, executor=PD, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4,
+                          fp64_quarters=2)
+        check(run(c, x, dev), bref, sc)
+    for d in (matgen_mod.banded(1, 1, seed=2, mean_degree=0.0), matgen_mod.banded(300, 1, seed=1, mean_degree=0.0)):
+        s = R.race_build(d, 4)
+        R.race_set_launch(s, 0, executor=PD, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4)
+        xx = matgen_mod.uniform(d["n"], 3)
+        bref, sc = oracle_mod.spmv_full(oracle_mod.expand_full(d), xx)
+        check(run(s, xx, dev), bref, sc)
