@@ -486,6 +486,9 @@ def run_ours(args):
     R.race_set_launch(s_cf, 0, R.RACE_EXEC_PERSIST_GROUP, 8, 1, 0, 8)
     t_persist_group = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), 3, 1)
     R.race_poll_status(s_cf, stream)  # raises if a grid barrier gave up
+    # the headline's arithmetic phase by phase, each leaf spread over the GPU
+    R.race_set_launch(s_cf, 0, **dict(lc, executor=R.RACE_EXEC_PHASE_DF64))
+    t_phase_cf = timed(lambda i: R.symm_spmv(s_cf, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
     s_cf.free()
     # ---- the paper's comparison methods, multicolouring (MC) and algebraic block
     # multicolouring (ABMC, blocks of 64 rows), under the same conflict-free executors --------
@@ -501,9 +504,11 @@ def run_ours(args):
             R.race_set_launch(sc, 0, R.RACE_EXEC_PERSIST_CTA, 1, 1, 0, 8)
             t_cp = timed(lambda i: R.symm_spmv(sc, xs[i % RING], bs[i % RING], stream), 3, 1)
             R.race_poll_status(sc, stream)
+            R.race_set_launch(sc, 0, **dict(lc, executor=R.RACE_EXEC_PHASE_DF64))
+            t_cd = timed(lambda i: R.symm_spmv(sc, xs[i % RING], bs[i % RING], stream), args.steps, args.warmup)
             colourings[label] = {"colours": ic["n_phases"], "leaves": ic["n_leaves"], "eta": ic["eta"],
                                  "leaf_cta_ms_per_step": t_c / 3 * 1e3, "persist_cta_ms_per_step": t_cp / 3 * 1e3,
-                                 "build_seconds": bsec}
+                                 "phase_df64_ms_per_step": t_cd / args.steps * 1e3, "build_seconds": bsec}
             sc.free()
     # ---- the same two kernels on the input order (no RACE permutation) --------------------
     s_nat = R.race_build(m, cfg["n_workers"], natural_order=True, windows=False, stream=stream)
@@ -683,6 +688,7 @@ def run_ours(args):
                           "what": "the same launches on the input order (RACE_FLAG_NATURAL_ORDER: no permutation)"},
         "race_conflict_free": {"leaf_cta_ms_per_step": t_leaf_cta / 3 * 1e3,
                                "persist_cta_ms_per_step": t_persist_cta / 3 * 1e3,
+                               "phase_df64_ms_per_step": t_phase_cf / args.steps * 1e3,
                                "leaf_group8_ms_per_step": t_leaf_group / 3 * 1e3,
                                "persist_group8_ms_per_step": t_persist_group / 3 * 1e3,
                                "window_race_ms_per_step": t_win_race / 3 * 1e3,
@@ -692,11 +698,13 @@ def run_ours(args):
                                             "eta": info_cf["eta"]},
                                "colourings": colourings,
                                "what": "RACE_EXEC_LEAF_CTA, _WINDOW_RACE, _LEAF_GROUP (8 lanes a leaf, plain "
-                                       "updates of b) and the one-launch _PERSIST_CTA / _PERSIST_GROUP (grid "
-                                       "barriers between phases) -- phase by phase, no two concurrent leaves share "
+                                       "updates of b), the one-launch _PERSIST_CTA / _PERSIST_GROUP (grid "
+                                       "barriers between phases) and _PHASE_DF64 (the headline's arithmetic, each "
+                                       "leaf spread over the GPU) -- phase by phase, no two concurrent leaves share "
                                        "an entry of b; x and b in that schedule's order -- on a fully recursed "
-                                       "schedule, 3 steps each; the leaf-per-block executors on the in-house MC "
-                                       "and ABMC colourings (race_build_coloring)"},
+                                       "schedule (3 steps each, PHASE_DF64 the bench's steps); the leaf-per-block "
+                                       "and phase executors on the in-house MC and ABMC colourings "
+                                       "(race_build_coloring)"},
         "speedup_vs_full": t_full / t_symm,
         "matrix_powers": mpk,
         "reduction_paths": red_paths,

@@ -315,12 +315,13 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    groups' transposed products in FP64, the
                                    rest double-float) phase by phase: one
                                    launch per phase over the rows of the
-                                   phase's leaves, cut into chunks of at most
-                                   256 rows of one leaf, a block per chunk at
-                                   a time.  No two concurrently running
-                                   leaves share an entry of b; the rows of
-                                   one leaf may run in different blocks, so
-                                   updates inside a leaf are L2 reductions.
+                                   phase's leaves (a list of them built with
+                                   the schedule, 4 bytes per row), 256 rows
+                                   a block at a time.  No two concurrently
+                                   running leaves share an entry of b; the
+                                   rows of one leaf may run in different
+                                   blocks, so updates inside a leaf are L2
+                                   reductions.
                                    blocks_per_sm, regs_per_row (4 or 8) as
                                    for DF64_RED; SymmSpMM runs DF64_RED's
                                    row-parallel kernel.  Same range check

@@ -139,25 +139,21 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
 }
 
 // One phase of the schedule (executor RACE_EXEC_PHASE_DF64): the rows of the
-// phase's leaves, cut into chunks of at most kBlock consecutive rows of one
-// leaf (chunks[q] = {first row, row count}); a block takes a chunk, one row
-// per thread, and the blocks take the chunks in turn.  The rows of one leaf
+// phase's leaves (rows[0, nrows), leaf after leaf), one per thread, a block
+// per 256 of them and the blocks taking those in turn.  The rows of one leaf
 // may run in different blocks, so their updates of shared entries of b are
 // L2 reductions; the leaves of a phase never share an entry of b (Sec. 4.2),
 // and the phases run in order, one launch each.
 template <typename VT, int B>
-__global__ void __launch_bounds__(kBlock) k_symm_df64_phase(const int2* __restrict__ chunks, int32_t nchunks,
+__global__ void __launch_bounds__(kBlock) k_symm_df64_phase(const int32_t* __restrict__ rows, int32_t nrows,
                                                            const int32_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
                                                            const VT* __restrict__ val, const double* __restrict__ x,
-                                                           double* b, int fp64_quarters, uint32_t chunk_base) {
-    for (int32_t q = blockIdx.x; q < nchunks; q += gridDim.x) {
-        const int2 ch = __ldg(chunks + q);
-        const bool warp64 = fp64_group((chunk_base + static_cast<uint32_t>(q)) * (kBlock / 32) + (threadIdx.x >> 5),
-                                       fp64_quarters);
-        if (static_cast<int32_t>(threadIdx.x) < ch.y)
-            row_df64<VT, 1, B>(ch.x + static_cast<int32_t>(threadIdx.x), 0, 1u << (threadIdx.x & 31), warp64, rp,
-                               col, val, x, b);
+                                                           double* b, int fp64_quarters, uint32_t group_base) {
+    for (int32_t q = blockIdx.x; static_cast<int64_t>(q) * kBlock < nrows; q += gridDim.x) {
+        const int32_t i = q * kBlock + static_cast<int32_t>(threadIdx.x);
+        const bool warp64 = fp64_group(group_base + static_cast<uint32_t>(i >> 5), fp64_quarters);
+        if (i < nrows) row_df64<VT, 1, B>(__ldg(rows + i), 0, 1u << (threadIdx.x & 31), warp64, rp, col, val, x, b);
     }
 }
 
@@ -225,21 +221,22 @@ int race_df64_phase_launch(const race_schedule* s, const double* x, double* b, c
     const int64_t cap = static_cast<int64_t>(sm_count_of_device()) * per_sm;
     const int q64 = mine ? s->launch.fp64_quarters : 0;
     const bool b8 = mine && s->launch.regs_per_row >= 8;
-    const auto& cp = s->chunk_ptr;
-    for (size_t p = 0; p + 1 < cp.size(); ++p) {
-        const int64_t nch = cp[p + 1] - cp[p];
-        if (nch == 0) continue;
-        const int grid = static_cast<int>(std::min(nch, cap));
-        const int2* ch = s->d_chunks + cp[p];
-        const uint32_t base = static_cast<uint32_t>(cp[p]);
+    const auto& pp = s->phase_row_ptr;
+    for (size_t p = 0; p + 1 < pp.size(); ++p) {
+        const int64_t nr = pp[p + 1] - pp[p];
+        if (nr == 0) continue;
+        const int grid = static_cast<int>(std::min((nr + kBlock - 1) / kBlock, cap));
+        const int32_t* rows = s->d_phase_rows + pp[p];
+        const int32_t nr32 = static_cast<int32_t>(nr);
+        const uint32_t base = static_cast<uint32_t>(pp[p] >> 5);
         if (s->val_type == RACE_F64) {
             const double* v = static_cast<const double*>(s->d_val);
-            if (b8) k_symm_df64_phase<double, 8><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
-            else k_symm_df64_phase<double, 4><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
+            if (b8) k_symm_df64_phase<double, 8><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
+            else k_symm_df64_phase<double, 4><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
         } else {
             const float* v = static_cast<const float*>(s->d_val);
-            if (b8) k_symm_df64_phase<float, 8><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
-            else k_symm_df64_phase<float, 4><<<grid, kBlock, 0, st>>>(ch, static_cast<int32_t>(nch), s->d_rp, s->d_col, v, x, b, q64, base);
+            if (b8) k_symm_df64_phase<float, 8><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
+            else k_symm_df64_phase<float, 4><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
         }
     }
     const cudaError_t e = cudaGetLastError();

@@ -29,13 +29,13 @@ int cuda_fail(cudaError_t e, const char* what) {
 void release_device(race_schedule* s) {
     void* ptrs[] = {s->d_rp, s->d_col, s->d_val, s->d_leaf_lo, s->d_leaf_hi, s->d_perm,
                     s->d_frp, s->d_fcol, s->d_fval, s->d_blk, s->d_fblk, s->d_status,
-                    s->mpk.d_reach, s->mpk.d_flags, s->d_stage, s->d_bar, s->d_chunks};
+                    s->mpk.d_reach, s->mpk.d_flags, s->d_stage, s->d_bar, s->d_phase_rows};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     s->mpk = MpkState();
     s->d_stage = nullptr;
     s->d_bar = nullptr;
-    s->d_chunks = nullptr;
+    s->d_phase_rows = nullptr;
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
@@ -225,18 +225,18 @@ static int upload_schedule(race_schedule* s, cudaStream_t st) {
     }
     if (rc == RACE_OK) rc = upload(s->plan.stage_ptr, &s->d_stage, st);
     if (rc == RACE_OK) {
-        // the phases' rows in chunks of at most kPhaseChunkRows rows of one leaf
+        // the rows of every phase's leaves, phase after phase
         const auto& sp = s->plan.stage_ptr;
-        std::vector<int2> ch;
-        s->chunk_ptr.assign(1, 0);
+        std::vector<int32_t> rows;
+        rows.reserve(static_cast<size_t>(n_rows));
+        s->phase_row_ptr.assign(1, 0);
         for (size_t p = 0; p + 1 < sp.size(); ++p) {
             for (int32_t q = sp[p]; q < sp[p + 1]; ++q)
-                for (int32_t r0 = s->plan.leaf_lo[static_cast<size_t>(q)]; r0 < s->plan.leaf_hi[static_cast<size_t>(q)];
-                     r0 += kPhaseChunkRows)
-                    ch.push_back(make_int2(r0, std::min(kPhaseChunkRows, s->plan.leaf_hi[static_cast<size_t>(q)] - r0)));
-            s->chunk_ptr.push_back(static_cast<int64_t>(ch.size()));
+                for (int32_t r = s->plan.leaf_lo[static_cast<size_t>(q)]; r < s->plan.leaf_hi[static_cast<size_t>(q)]; ++r)
+                    rows.push_back(r);
+            s->phase_row_ptr.push_back(static_cast<int64_t>(rows.size()));
         }
-        rc = upload(ch, &s->d_chunks, st);
+        rc = upload(rows, &s->d_phase_rows, st);
     }
     if (rc == RACE_OK) {
         // barrier words, a leaf ticket per phase, block-ranking counters

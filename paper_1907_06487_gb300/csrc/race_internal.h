@@ -154,10 +154,10 @@ struct race_schedule {
     int64_t n_fblk = 0;
     int32_t* d_status = nullptr;  // device status word (RACE_ERR_TIMEOUT)
     int32_t* d_stage = nullptr;   // plan.stage_ptr on the device (one-launch executors)
-    // the phases' rows in chunks of at most 256 rows of one leaf, {first row,
-    // count}, phase by phase (RACE_EXEC_PHASE_DF64); chunk_ptr[p] = first of phase p
-    std::vector<int64_t> chunk_ptr;
-    int2* d_chunks = nullptr;
+    // the rows of every phase's leaves, phase after phase (RACE_EXEC_PHASE_DF64);
+    // phase_row_ptr[p] = the first of phase p
+    std::vector<int64_t> phase_row_ptr;
+    int32_t* d_phase_rows = nullptr;
     uint32_t* d_bar = nullptr;    // one-launch executors: barrier words, leaf tickets, block ranking
     int32_t max_row_upper = 0, max_row_full = 0;
     WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
@@ -195,8 +195,6 @@ int race_df64_prepare(const race_schedule* s);
 int race_df64_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
 // The double-float arithmetic phase by phase (RACE_EXEC_PHASE_DF64).
 int race_df64_phase_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
-// Rows per chunk of RACE_EXEC_PHASE_DF64 (one block's threads).
-constexpr int32_t kPhaseChunkRows = 256;
 
 // SELL executor (sell_kernels.cu): layout construction, upload on first use,
 // release, launch.
