@@ -859,7 +859,8 @@ def mpk_block(R, pm, s, n, nu, dev, stream, timed, steps, peak, p=4):
 def sweeps_block(args, R, configs, pm, dev, stream, timed, peak):
     """Symmetric Gauss-Seidel and symmetric Kaczmarz sweeps on the 27-point
     stencil under the fully recursed schedule the leaf executors use (the
-    paper's execution model: phases in order, one leaf per lane group)."""
+    paper's execution model: phases in order, one leaf per lane group), and
+    under the in-house MC and ABMC colourings."""
     import torch
     name = "st27_200"
     m = configs.matrix(name)
@@ -885,6 +886,25 @@ def sweeps_block(args, R, configs, pm, dev, stream, timed, peak):
         out[label] = {"ms_per_sweep": t * 1e3, "gbs": pm.sweep_bytes(n, nf) / t / 1e9,
                       "frac": pm.sweep_bytes(n, nf) / t / 1e9 / peak}
     s.free()
+    # the same sweeps under the in-house multicolourings (one-row leaves for MC,
+    # 16-row blocks for ABMC, both on the RCM order): every row of a colour in
+    # parallel, a small lane group per leaf
+    for label, method, block, lanes in (("mc", R.RACE_COLOR_MC, 1, 2), ("abmc16", R.RACE_COLOR_ABMC, 16, 4)):
+        t0c = time.perf_counter()
+        sc = R.race_build_coloring(m, method, block, stream=stream, windows=False, rcm=True)
+        R.race_prepare_full(sc, stream)
+        bsec = time.perf_counter() - t0c
+        ic = sc.info()
+        R.race_set_launch(sc, 0, executor=R.RACE_EXEC_LEAF_GROUP, group_lanes=lanes, rows_per_group=1,
+                          blocks_per_sm=0, regs_per_row=8)
+        blk = {"colours": ic["n_phases"], "leaves": ic["n_leaves"], "group_lanes": lanes, "build_seconds": bsec}
+        for kl, fn in (("symm_gs", R.symm_gs), ("symm_kacz", R.symm_kacz)):
+            fn(sc, b, x, 1, stream)
+            t = timed(lambda i: fn(sc, b, x, sweeps, stream), 1, 1) / sweeps
+            blk[kl] = {"ms_per_sweep": t * 1e3, "gbs": pm.sweep_bytes(n, nf) / t / 1e9,
+                       "frac": pm.sweep_bytes(n, nf) / t / 1e9 / peak}
+        out[label] = blk
+        sc.free()
     del b, x
     torch.cuda.empty_cache()
     return out

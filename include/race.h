@@ -460,7 +460,11 @@ int spmv_full(const race_schedule *s, const double *x_d, double *b_d, void *stre
  * is the serial sweep in that execution order.  b_d (input) and x_d (start
  * value in, result out) are caller-owned device arrays of n doubles in
  * permuted order and must not alias; the full CRS is built on first use as
- * for spmv_full.  One launch per phase and pass on `stream`.  A zero
+ * for spmv_full.  One launch per phase and pass on `stream`; each leaf runs
+ * on a group of the schedule's group_lanes lanes (race_set_launch; 1, 2,
+ * 4, 8, 16 or 32), four entries a lane per step.  Colourings with leaves of
+ * one or a few rows (race_build_coloring) keep every lane busy; RACE's
+ * leaves of many rows are chains of dependent row updates.  A zero
  * diagonal gives inf or nan entries.
  * Errors: RACE_ERR_INVALID (NULL, aliasing, sweeps < 0), _UNSUPPORTED
  * (host-only schedule), _OVERFLOW, _NOMEM, _CUDA.                          */

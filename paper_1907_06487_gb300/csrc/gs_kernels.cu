@@ -58,15 +58,29 @@ __global__ void __launch_bounds__(kBlock) k_gs_phase(const int32_t* __restrict__
         const int32_t r = BACKWARD ? hi - 1 - k : lo + k;
         double s = 0.0, d = 0.0;  // Gauss-Seidel: off-diagonal sum, diagonal; Kaczmarz: a.x, |a|^2
         const int32_t beg = __ldg(frp + r), end = __ldg(frp + r + 1);
-        for (int32_t t = beg + lane; t < end; t += G) {
-            const int32_t c = __ldg(fcol + t);
-            const double a = static_cast<double>(__ldg(fval + t));
-            if constexpr (KACZ) {
-                s += a * x[c];  // plain load: x changes during the launch
-                d += a * a;
-            } else {
-                if (c == r) d += a;
-                else s += a * x[c];
+        // U entries per lane and step, all loads of a step issued before their uses
+        constexpr int U = 4;
+        for (int32_t t0 = beg + lane; t0 < end; t0 += U * G) {
+            int32_t c[U];
+            double a[U], xc[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t t = t0 + u * G;
+                c[u] = t < end ? __ldg(fcol + t) : -1;
+                a[u] = t < end ? static_cast<double>(__ldg(fval + t)) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xc[u] = c[u] >= 0 ? x[c[u]] : 0.0;  // plain loads: x changes during the launch
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] < 0) continue;
+                if constexpr (KACZ) {
+                    s += a[u] * xc[u];
+                    d += a[u] * a[u];
+                } else {
+                    if (c[u] == r) d += a[u];
+                    else s += a[u] * xc[u];
+                }
             }
         }
 #pragma unroll
@@ -108,6 +122,8 @@ void sweep(const race_schedule* s, const double* b, double* x, int32_t sweeps, c
 template <typename VT, bool KACZ>
 void sweep_vt(const race_schedule* s, const double* b, double* x, int32_t sweeps, cudaStream_t st) {
     switch (s->group_lanes) {
+        case 1: sweep<VT, 1, KACZ>(s, b, x, sweeps, st); break;
+        case 2: sweep<VT, 2, KACZ>(s, b, x, sweeps, st); break;
         case 4: sweep<VT, 4, KACZ>(s, b, x, sweeps, st); break;
         case 16: sweep<VT, 16, KACZ>(s, b, x, sweeps, st); break;
         case 32: sweep<VT, 32, KACZ>(s, b, x, sweeps, st); break;

@@ -134,3 +134,43 @@ def test_symm_kacz_refuses_one_level_stage0(dev, matgen_mod):
     torch.cuda.synchronize()
     assert torch.all(x == 0.0)  # nothing ran
     R.symm_gs(s, b, x, 1)  # Gauss-Seidel needs distance 1 only: accepted
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("sched", ["race", "mc", "abmc8"])
+def test_sweeps_every_lane_count(dev, oracle_mod, matgen_mod, sched, lanes):
+    """Both sweeps with every lane-group width, on a RACE schedule (leaves of
+    many rows: the rows of a leaf one after the other) and on the MC and ABMC
+    colourings (leaves of one and of 8 rows), against the oracle on the same
+    schedule; rows of up to 27 entries span one or several steps of four
+    entries a lane."""
+    m = matgen_mod.stencil3d(12, npt=27, seed=5)
+    if sched == "race":
+        s = R.race_build(m, 32, max_depth=-1)
+    elif sched == "mc":
+        s = R.race_build_coloring(m, R.RACE_COLOR_MC, 1)
+    else:
+        s = R.race_build_coloring(m, R.RACE_COLOR_ABMC, 8)
+    R.race_set_launch(s, 0, executor=R.RACE_EXEC_LEAF_GROUP, group_lanes=lanes, rows_per_group=1, blocks_per_sm=0,
+                      regs_per_row=8)
+    full = oracle_mod.expand_full(s.matrix())
+    sp, lo, hi = s.phases()
+    n = m["n"]
+    rng = np.random.default_rng(17)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    bd = torch.from_numpy(b).to(dev)
+    want = oracle_mod.symm_gs(full, sp, lo, hi, b, x0, 2)
+    xd = torch.from_numpy(x0.copy()).to(dev)
+    R.symm_gs(s, bd, xd, 2)
+    torch.cuda.synchronize()
+    got = xd.cpu().numpy()
+    bound = 1e-12 * dense_scale(full, want, b)
+    assert np.all(np.abs(got - want) <= bound), float(np.max(np.abs(got - want) / bound))
+    want = oracle_mod.symm_kacz(full, sp, lo, hi, b, x0, 2)
+    xd = torch.from_numpy(x0.copy()).to(dev)
+    R.symm_kacz(s, bd, xd, 2)
+    torch.cuda.synchronize()
+    got = xd.cpu().numpy()
+    mag = np.abs(want) + np.abs(x0)
+    local = np.maximum(np.maximum.reduceat(mag[full["col"]], full["row_ptr"][:-1]), mag)
+    assert np.all(np.abs(got - want) <= 1e-12 * local), float(np.max(np.abs(got - want) / local))
