@@ -140,20 +140,27 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
 
 // One phase of the schedule (executor RACE_EXEC_PHASE_DF64): the rows of the
 // phase's leaves (rows[0, nrows), leaf after leaf), one per thread, a block
-// per 256 of them and the blocks taking those in turn.  The rows of one leaf
-// may run in different blocks, so their updates of shared entries of b are
-// L2 reductions; the leaves of a phase never share an entry of b (Sec. 4.2),
-// and the phases run in order, one launch each.
+// per 256 of them and the blocks taking those in turn; first[q] is the first
+// row of the q-th 256 when they are consecutive rows (no list to read), else
+// -1.  The rows of one leaf may run in different blocks, so their updates of
+// shared entries of b are L2 reductions; the leaves of a phase never share
+// an entry of b (Sec. 4.2), and the phases run in order, one launch each.
 template <typename VT, int B>
-__global__ void __launch_bounds__(kBlock) k_symm_df64_phase(const int32_t* __restrict__ rows, int32_t nrows,
+__global__ void __launch_bounds__(kBlock) k_symm_df64_phase(const int32_t* __restrict__ rows,
+                                                           const int32_t* __restrict__ first, int32_t nrows,
                                                            const int32_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
                                                            const VT* __restrict__ val, const double* __restrict__ x,
                                                            double* b, int fp64_quarters, uint32_t group_base) {
+    static_assert(kBlock == kPhaseBlockRows, "a block takes one entry of the first-row table");
     for (int32_t q = blockIdx.x; static_cast<int64_t>(q) * kBlock < nrows; q += gridDim.x) {
         const int32_t i = q * kBlock + static_cast<int32_t>(threadIdx.x);
         const bool warp64 = fp64_group(group_base + static_cast<uint32_t>(i >> 5), fp64_quarters);
-        if (i < nrows) row_df64<VT, 1, B>(__ldg(rows + i), 0, 1u << (threadIdx.x & 31), warp64, rp, col, val, x, b);
+        const int32_t f = __ldg(first + q);
+        if (i < nrows) {
+            const int32_t row = f >= 0 ? f + static_cast<int32_t>(threadIdx.x) : __ldg(rows + i);
+            row_df64<VT, 1, B>(row, 0, 1u << (threadIdx.x & 31), warp64, rp, col, val, x, b);
+        }
     }
 }
 
@@ -227,16 +234,17 @@ int race_df64_phase_launch(const race_schedule* s, const double* x, double* b, c
         if (nr == 0) continue;
         const int grid = static_cast<int>(std::min((nr + kBlock - 1) / kBlock, cap));
         const int32_t* rows = s->d_phase_rows + pp[p];
+        const int32_t* first = s->d_phase_blk + s->phase_blk_ptr[p];
         const int32_t nr32 = static_cast<int32_t>(nr);
         const uint32_t base = static_cast<uint32_t>(pp[p] >> 5);
         if (s->val_type == RACE_F64) {
             const double* v = static_cast<const double*>(s->d_val);
-            if (b8) k_symm_df64_phase<double, 8><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
-            else k_symm_df64_phase<double, 4><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
+            if (b8) k_symm_df64_phase<double, 8><<<grid, kBlock, 0, st>>>(rows, first, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
+            else k_symm_df64_phase<double, 4><<<grid, kBlock, 0, st>>>(rows, first, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
         } else {
             const float* v = static_cast<const float*>(s->d_val);
-            if (b8) k_symm_df64_phase<float, 8><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
-            else k_symm_df64_phase<float, 4><<<grid, kBlock, 0, st>>>(rows, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
+            if (b8) k_symm_df64_phase<float, 8><<<grid, kBlock, 0, st>>>(rows, first, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
+            else k_symm_df64_phase<float, 4><<<grid, kBlock, 0, st>>>(rows, first, nr32, s->d_rp, s->d_col, v, x, b, q64, base);
         }
     }
     const cudaError_t e = cudaGetLastError();

@@ -29,13 +29,14 @@ int cuda_fail(cudaError_t e, const char* what) {
 void release_device(race_schedule* s) {
     void* ptrs[] = {s->d_rp, s->d_col, s->d_val, s->d_leaf_lo, s->d_leaf_hi, s->d_perm,
                     s->d_frp, s->d_fcol, s->d_fval, s->d_blk, s->d_fblk, s->d_status,
-                    s->mpk.d_reach, s->mpk.d_flags, s->d_stage, s->d_bar, s->d_phase_rows};
+                    s->mpk.d_reach, s->mpk.d_flags, s->d_stage, s->d_bar, s->d_phase_rows, s->d_phase_blk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     s->mpk = MpkState();
     s->d_stage = nullptr;
     s->d_bar = nullptr;
     s->d_phase_rows = nullptr;
+    s->d_phase_blk = nullptr;
     s->d_rp = s->d_col = s->d_leaf_lo = s->d_leaf_hi = s->d_perm = s->d_frp = s->d_fcol = nullptr;
     s->d_blk = s->d_fblk = s->d_status = nullptr;
     s->d_val = s->d_fval = nullptr;
@@ -236,7 +237,20 @@ static int upload_schedule(race_schedule* s, cudaStream_t st) {
                     rows.push_back(r);
             s->phase_row_ptr.push_back(static_cast<int64_t>(rows.size()));
         }
+        // per block of 256 rows of a phase: its first row if the rows are consecutive
+        std::vector<int32_t> blk;
+        s->phase_blk_ptr.assign(1, 0);
+        for (size_t p = 0; p + 1 < s->phase_row_ptr.size(); ++p) {
+            for (int64_t i0 = s->phase_row_ptr[p]; i0 < s->phase_row_ptr[p + 1]; i0 += kPhaseBlockRows) {
+                const int64_t i1 = std::min<int64_t>(i0 + kPhaseBlockRows, s->phase_row_ptr[p + 1]);
+                bool run = true;
+                for (int64_t i = i0 + 1; i < i1 && run; ++i) run = rows[static_cast<size_t>(i)] == rows[static_cast<size_t>(i - 1)] + 1;
+                blk.push_back(run ? rows[static_cast<size_t>(i0)] : -1);
+            }
+            s->phase_blk_ptr.push_back(static_cast<int64_t>(blk.size()));
+        }
         rc = upload(rows, &s->d_phase_rows, st);
+        if (rc == RACE_OK) rc = upload(blk, &s->d_phase_blk, st);
     }
     if (rc == RACE_OK) {
         // barrier words, a leaf ticket per phase, block-ranking counters

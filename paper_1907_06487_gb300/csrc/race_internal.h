@@ -155,9 +155,12 @@ struct race_schedule {
     int32_t* d_status = nullptr;  // device status word (RACE_ERR_TIMEOUT)
     int32_t* d_stage = nullptr;   // plan.stage_ptr on the device (one-launch executors)
     // the rows of every phase's leaves, phase after phase (RACE_EXEC_PHASE_DF64);
-    // phase_row_ptr[p] = the first of phase p
-    std::vector<int64_t> phase_row_ptr;
+    // phase_row_ptr[p] = the first of phase p.  Per 256 of a phase's rows (one
+    // block's share, phase_blk_ptr[p] = the first of phase p), d_phase_blk
+    // holds their first row when they are consecutive rows, else -1.
+    std::vector<int64_t> phase_row_ptr, phase_blk_ptr;
     int32_t* d_phase_rows = nullptr;
+    int32_t* d_phase_blk = nullptr;
     uint32_t* d_bar = nullptr;    // one-launch executors: barrier words, leaf tickets, block ranking
     int32_t max_row_upper = 0, max_row_full = 0;
     WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
@@ -195,6 +198,8 @@ int race_df64_prepare(const race_schedule* s);
 int race_df64_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
 // The double-float arithmetic phase by phase (RACE_EXEC_PHASE_DF64).
 int race_df64_phase_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
+// Rows of a phase one block of RACE_EXEC_PHASE_DF64 takes at a time.
+constexpr int32_t kPhaseBlockRows = 256;
 
 // SELL executor (sell_kernels.cu): layout construction, upload on first use,
 // release, launch.
