@@ -10,10 +10,10 @@ eps_0, eps_1 in {0.5, 0.6, 0.7, 0.8, 0.9} x depth in {1, 2, 3, 4, unlimited}
 (eps_s = 0.5 for s > 1) is swept, each point timed on the GPU with the
 schedule-bound executor (RACE_EXEC_LEAF_GROUP: one RACE leaf per lane group,
 plain stores, one launch per phase), and the fastest point is the label.
-The exhaustive sweep stays both the fallback and the judge of the
+The exhaustive sweep stays both the fallback and the measure of the
 predictor's regret.
 
-A second data set (dataset_matrix_v2, config sizes: stencils of side 16..128,
+A second data set (dataset_matrix_v2, full sizes: stencils of side 16..128,
 XXZ L = 16..24, geometric and band matrices of 10^4..10^6 rows) is swept over
 GRID_V2 with the executors that run all rows at once (the library's default)
 and one leaf per block, N_t = 152; a network is trained per executor.  Every
