@@ -23,6 +23,7 @@ point chosen on the training matrices beside the network.
 Usage (GPU):  python -m paper_1907_06487_gb300.predictor sweep        (data/predictor_sweep.npz)
               python -m paper_1907_06487_gb300.predictor train        (data/predictor.f32)
               python -m paper_1907_06487_gb300.predictor sweep_full   (data/predictor_sweep_full.npz)
+              python -m paper_1907_06487_gb300.predictor sweep_full_phased (adds the phase-by-phase labels)
               python -m paper_1907_06487_gb300.predictor train_full   (data/predictor_full_*.f32)
 """
 from __future__ import annotations
@@ -120,6 +121,10 @@ SWEEP_WORKERS_V2 = 152
 V2_LAUNCH = {"default": dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4,
                              fp64_quarters=2),
              "leafcta": dict(executor=1, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=8)}
+# a third label set, added to the same data set later: the default arithmetic
+# run phase by phase (RACE_EXEC_PHASE_DF64), where the number of phases counts
+V2_LAUNCH_PHASED = {"phased": dict(executor=13, group_lanes=1, rows_per_group=1, blocks_per_sm=0, regs_per_row=4,
+                                   fp64_quarters=2)}
 
 
 def dataset_matrix_v2(i, count=500, seed=10):
@@ -184,14 +189,15 @@ def _sweep_one(args):
 
 
 def _sweep_one_v2(args):
-    """Worker: every point of GRID_V2 for matrix i, timed with both executors
-    (depth-1 points share one schedule across eps_1, which stage 0 ignores)."""
-    i, count, reps = args
+    """Worker: every point of GRID_V2 for matrix i, timed with each of the
+    given launches (depth-1 points share one schedule across eps_1, which
+    stage 0 ignores)."""
+    i, count, reps, launches = args
     import torch
     from . import race_set_launch, race_upload, symm_spmv
     name, m = dataset_matrix_v2(i, count)
     feats = race_features(m)
-    out = {k: np.zeros(len(GRID_V2)) for k in V2_LAUNCH}
+    out = {k: np.zeros(len(GRID_V2)) for k in launches}
     with _GPU_LOCK:
         xd = torch.rand(m["n"], dtype=torch.float64, device="cuda:0")
         bd = torch.empty_like(xd)
@@ -200,14 +206,14 @@ def _sweep_one_v2(args):
     for j, (e0, e1, d) in enumerate(GRID_V2.points):
         key = (e0, e1 if d != 1 else None, d)
         if key in done:
-            for k in V2_LAUNCH:
+            for k in launches:
                 out[k][j] = out[k][done[key]]
             continue
         done[key] = j
         s = race_build(m, SWEEP_WORKERS_V2, eps=(e0, e1, 0.5), max_depth=d, host_only=True, windows=False)
         with _GPU_LOCK:
             race_upload(s)
-            for k, launch in V2_LAUNCH.items():
+            for k, launch in launches.items():
                 race_set_launch(s, 0, **launch)
                 # one timed call sizes the repetitions: about 1 ms of work per point,
                 # at least `reps` calls, so that short kernels are not launch noise
@@ -232,29 +238,41 @@ def _sweep_one_v2(args):
     return i, name, feats, out
 
 
-def sweep_v2(count=500, out_path=None, log=sys.stderr, workers=None, reps=6):
-    """Full-size sweep over GRID_V2 with both executors; saves features, times."""
+def sweep_v2(count=500, out_path=None, log=sys.stderr, workers=None, reps=6, launches=None, add=False):
+    """Full-size sweep over GRID_V2, each point timed with every launch of
+    `launches` (default: V2_LAUNCH); saves features and times_<label> arrays.
+    add=True keeps the arrays already in the file (same matrices and grid)
+    and adds the new labels to it."""
     import multiprocessing as mp
+    launches = launches or V2_LAUNCH
     workers = workers or min(16, os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
     lock = ctx.Lock()
     feats = np.zeros((count, 16), np.float32)
-    times = {k: np.zeros((count, len(GRID_V2)), np.float64) for k in V2_LAUNCH}
+    times = {k: np.zeros((count, len(GRID_V2)), np.float64) for k in launches}
     names = [""] * count
     t0 = time.time()
     with ctx.Pool(workers, initializer=_init_worker, initargs=(lock,)) as pool:
-        for c, (i, name, f, t) in enumerate(pool.imap_unordered(_sweep_one_v2, [(i, count, reps) for i in range(count)])):
+        jobs = [(i, count, reps, launches) for i in range(count)]
+        for c, (i, name, f, t) in enumerate(pool.imap_unordered(_sweep_one_v2, jobs)):
             feats[i], names[i] = f, name
-            for k in V2_LAUNCH:
+            for k in launches:
                 times[k][i] = t[k]
             if c % 25 == 0:
-                print(f"sweep_v2 {c}/{count} {name} default best {t['default'].min()*1e6:.1f} us "
-                      f"leafcta best {t['leafcta'].min()*1e6:.1f} us  {time.time()-t0:.0f} s", file=log, flush=True)
+                best = "  ".join(f"{k} best {t[k].min()*1e6:.1f} us" for k in launches)
+                print(f"sweep_v2 {c}/{count} {name} {best}  {time.time()-t0:.0f} s", file=log, flush=True)
     out_path = out_path or os.path.join(DATA, "predictor_sweep_full.npz")
     os.makedirs(os.path.dirname(out_path), exist_ok=True)
-    np.savez_compressed(out_path, features=feats, times_default=times["default"], times_leafcta=times["leafcta"],
-                        names=np.array(names), grid=np.array(GRID_V2.points, dtype=np.float64),
-                        workers=SWEEP_WORKERS_V2)
+    arrays = {}
+    if add and os.path.exists(out_path):
+        old = np.load(out_path)
+        arrays = {k: old[k] for k in old.files}
+        if not (np.array_equal(arrays["names"], np.array(names)) and
+                np.array_equal(arrays["grid"], np.array(GRID_V2.points, dtype=np.float64))):
+            raise ValueError("sweep_v2(add=True): the file holds another data set or grid")
+    arrays.update(features=feats, names=np.array(names), grid=np.array(GRID_V2.points, dtype=np.float64),
+                  workers=SWEEP_WORKERS_V2, **{"times_" + k: v for k, v in times.items()})
+    np.savez_compressed(out_path, **arrays)
     return feats, times, names
 
 
@@ -421,6 +439,9 @@ def main(argv):
     elif argv and argv[0] == "sweep_full":
         count = int(argv[1]) if len(argv) > 1 else 500
         sweep_v2(count)
+    elif argv and argv[0] == "sweep_full_phased":
+        count = int(argv[1]) if len(argv) > 1 else 500
+        sweep_v2(count, launches=V2_LAUNCH_PHASED, add=True)
     elif argv and argv[0] == "train":
         d = np.load(os.path.join(DATA, "predictor_sweep.npz"))
         pred, res = train_and_evaluate(d["features"], d["times"], GRID_V1)
@@ -428,7 +449,7 @@ def main(argv):
         print(res)
     elif argv and argv[0] == "train_full":
         d = np.load(os.path.join(DATA, "predictor_sweep_full.npz"))
-        for target in ("default", "leafcta"):
+        for target in [k[len("times_"):] for k in d.files if k.startswith("times_")]:
             pred, res = train_and_evaluate(d["features"], d["times_" + target], GRID_V2)
             pred.save(os.path.join(DATA, f"predictor_full_{target}.f32"))
             print(target, res)

@@ -91,11 +91,12 @@ def test_predictor_beats_paper_default_and_best_fixed_point_on_held_out():
     assert ev["mlp_mean"] < ev["fixed_mean"]
 
 
-@pytest.mark.parametrize("target", ["default", "leafcta"])
+@pytest.mark.parametrize("target", ["default", "leafcta", "phased"])
 def test_full_size_predictor_beats_default_and_best_fixed_point(target):
     """The full-size sweep (500 matrices of the paper-shaped families at their
     stated sizes, 64 grid points each, timed on a GB300 with the library's
-    default executor and with the leaf-per-block executor): on the 100
+    default executor, with the leaf-per-block executor and with the default
+    arithmetic run phase by phase): on the 100
     held-out matrices the network trained on the other 400 has a lower mean
     regret than the paper's fixed point (0.8, 0.8, unlimited depth) and than
     the best single grid point chosen on the 400 training matrices."""
