@@ -361,17 +361,28 @@ RING = 4  # x and b buffers rotated over the timed steps
 
 
 def arithmetic_label(launch):
-    """What the launch computes in: FP64, or FP64 row sums with a share of
-    double-float transposed products (the products' relative error is below
-    2^-44 each; x, b and the accumulation stay FP64)."""
+    """What the launch computes in: FP64 throughout, or FP64 row sums with a
+    share of the transposed products formed by an integer product of the
+    significands (a binary64 result: the exact product truncated, below two
+    units in the last place, relative error below 2^-51; x, b and the
+    accumulation stay FP64), or (staged executor) double-float row sums."""
     ex = launch.get("executor")
-    if ex in (8, 9):
+    if ex in (8, 9, 13):
         q = launch.get("fp64_quarters", 0)
-        return (f"f64 row sums; transposed products f64 in {q}/4 of the warps and double-float "
-                f"(Dekker products of FP32 halves, joined to f64 before the reduction) in {4 - q}/4")
+        return (f"f64 row sums; transposed products f64 multiplies in {q}/4 of the warps and in {4 - q}/4 "
+                f"f64 products formed on the integer pipes (significands multiplied in 32-bit pieces, "
+                f"truncated to 53 bits)")
     if ex == 10:
         return (f"row sums f64 in {launch.get('rowsum_fp64_quarters', 4)}/4 of the warps (rest double-float), "
-                f"transposed products f64 in {launch.get('fp64_quarters', 0)}/4 (rest double-float)")
+                f"transposed products f64 multiplies in {launch.get('fp64_quarters', 0)}/4 (rest formed on the "
+                f"integer pipes)")
+    return "f64"
+
+
+def dtype_label(launch):
+    """f64 unless the staged executor sums some rows in double-float."""
+    if launch.get("executor") == 10 and launch.get("rowsum_fp64_quarters", 4) < 4:
+        return "f64+df64"
     return "f64"
 
 
@@ -645,7 +656,7 @@ def run_ours(args):
         "metric": METRIC_SYMM,
         "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+df64" if lc["executor"] in (8, 9, 10) else "f64", "arithmetic": arithmetic_label(lc),
+        "dtype": dtype_label(lc), "arithmetic": arithmetic_label(lc),
         "data": "synthetic",
         "config": {"workload": name, "desc": WORKLOAD_DESC.get(name, name), "n": n, "nnz_upper": nu, "nnz_full": nf,
                    "l2": "inputs larger than L2 (matrix 1.05 GB; x, b rotate over 4+4 buffers of 83 MB)",
@@ -1107,7 +1118,7 @@ def run_batch(args):
             "metric": "SymmSpMM GFLOP/s (2*nnz_full*k flops) of a 64-matrix batch in one CUDA graph",
             "value": whole_job_rate(world, flops, args.steps, t) / 1e9, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+df64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "batch64", **{k: blk[k] for k in
                                                                       ("k", "matrices", "rows", "schedule",
                                                                        "tuned_launches", "l2")}},

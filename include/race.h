@@ -253,12 +253,16 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    entry of b (conflict-free, no atomics in
                                    global memory)                           */
 #define RACE_EXEC_DF64_RED  8   /* as ROWS_RED (group_lanes lanes per row):
-                                   FP64 row sums, and every transposed
-                                   update a_ij x_i formed in double-float
-                                   arithmetic on the FP32 and integer pipes
-                                   (relative error below 2^-44 each; the
-                                   result stays within 1e-12 sum_j
-                                   |a_ij x_j| of the exact one).  First use
+                                   FP64 row sums, and the transposed updates
+                                   a_ij x_i of (4 - fp64_quarters) of every
+                                   four row groups formed off the FP64 pipe
+                                   by an integer product of the two
+                                   significands (the exact product
+                                   truncated, relative error below 2^-51
+                                   each; the result stays within 1e-12
+                                   sum_j |a_ij x_j| of the exact one).  The
+                                   name is kept from the double-float
+                                   product this executor used first.  First use
                                    checks the off-diagonal values once and
                                    returns RACE_ERR_UNSUPPORTED if one is
                                    nonzero and outside [2^-50, 2^51) in
@@ -285,7 +289,8 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
                                    the warps the row sums run in FP64 or in
                                    double-float arithmetic
                                    (rowsum_fp64_quarters) and the transposed
-                                   products likewise (fp64_quarters); the
+                                   products in FP64 or by DF64_RED's integer
+                                   product (fp64_quarters); the
                                    result stays within 1e-12 sum_j
                                    |a_ij x_j| of the exact one.  Entries
                                    whose value or x lies outside
@@ -313,7 +318,8 @@ int symm_spmv(const race_schedule *s, const double *x_d, double *b_d, void *stre
 #define RACE_EXEC_PHASE_DF64 13 /* DF64_RED's arithmetic (one row per lane,
                                    FP64 row sums, fp64_quarters of the row
                                    groups' transposed products in FP64, the
-                                   rest double-float) phase by phase: one
+                                   rest by the integer product) phase by
+                                   phase: one
                                    launch per phase over the rows of the
                                    phase's leaves (a list of them built with
                                    the schedule, 4 bytes per row), 256 rows
@@ -343,8 +349,8 @@ typedef struct {
     int32_t fp64_quarters;   /* RACE_EXEC_DF64_RED (and its SymmSpMM): in
                                 this many of every four row iterations of a
                                 warp (0..4) the transposed updates use FP64
-                                multiplies, in the rest double-float
-                                arithmetic; shares the work between the
+                                multiplies, in the rest the integer product
+                                of the significands; shares the work between the
                                 FP64 and integer pipes, spread evenly over
                                 each SM's four FP64 units                */
     int32_t rowsum_fp64_quarters; /* RACE_EXEC_STAGED: in this many quarters
@@ -495,7 +501,7 @@ int symm_kacz(const race_schedule *s, const double *b_d, double *x_d, int32_t sw
  *     level couple only to the neighbouring levels, Sec. 4.1), so several
  *     powers advance together over the matrix.  Arithmetic as
  *     RACE_EXEC_DF64_RED with the schedule's fp64_quarters (all FP64 when a
- *     stored value lies outside the double-float range).  FP64-stored values
+ *     stored value lies outside [2^-50, 2^51)).  FP64-stored values
  *     only.  The first call builds the block table on the host and uploads
  *     it (allocates and waits for `stream`), and a call with a larger p than
  *     before allocates its done flags: make those calls outside stream
@@ -581,8 +587,8 @@ void race_batch_free(race_batch *b);
 /* race_autotune — times the candidate launch shapes (executors
  * RACE_EXEC_ROWS_RED, RACE_EXEC_PIPE_RED and, when the matrix's values are
  * in its range, RACE_EXEC_DF64_RED, with their lane, row and register
- * shapes, default and 4 blocks per SM, and 6 blocks per SM with 1 or 2
- * FP64 quarters for RACE_EXEC_DF64_RED) of symm_spmv (k == 1) or
+ * shapes, default and 4 blocks per SM, RACE_EXEC_DF64_RED also 6 blocks per
+ * SM, with 0, 1 or 2 FP64 quarters) of symm_spmv (k == 1) or
  * symm_spmm (k > 1) on the given buffers: one warm-up and `reps` timed
  * calls each, CUDA events on `stream`.  Keeps the fastest as the
  * schedule's launch shape and returns it in *best (and its time per call

@@ -43,12 +43,13 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # of the Gauss-Seidel and Kaczmarz sweeps (distance-2 phases throughout: the
 # Kaczmarz update writes every column of a row).
 # (sweeps of blocks per SM x entries per step x FP64 share on GB300: XXZ L=26
-# 6 blocks of 40-register threads, 4 entries, half of the row groups'
-# transposed products in FP64, 0.321 ms against 0.322-0.328 at 5 blocks or
-# share 1/4 and 0.348 at share 0; the 27-point stencil 4 blocks, 4 entries,
-# share 2/4, 0.366 ms against 0.372 at 8 entries per step)
-_L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=6, regs_per_row=4, fp64_quarters=2)
-_LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=4, fp64_quarters=2)
+# 6 blocks of 40-register threads, 4 entries; the 27-point stencil 4 blocks,
+# 4 entries (0.372 ms at 8 entries per step).  With the transposed products
+# formed by the integer product of the significands, a quarter of the row
+# groups' products in FP64: XXZ 0.311 ms against 0.315 at share 0 and 0.321
+# at 2/4; stencil 0.356 ms against 0.358 / 0.360)
+_L = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=6, regs_per_row=4, fp64_quarters=1)
+_LP = dict(executor=8, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=4, fp64_quarters=1)
 _F = dict(executor=2, group_lanes=1, rows_per_group=1, blocks_per_sm=4, regs_per_row=16)
 SCHEDULE = {
     "anderson32": dict(n_workers=64, eps=(0.8, 0.8, 0.5), max_depth=-1, executor=1, launch=_L, full_launch=_F),

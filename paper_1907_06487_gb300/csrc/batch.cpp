@@ -155,7 +155,8 @@ int race_autotune(race_schedule* s, int32_t k, const double* X_d, double* B_d, i
         return RACE_ERR_UNSUPPORTED;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the double-float executor competes when the matrix's values allow it
+    // the executor with the transposed products off the FP64 pipe competes
+    // when the matrix's values allow it
     const bool df = race_df64_prepare(s) == RACE_OK;
     std::vector<race_launch> cand;
     for (int bps : {0, 4, 6}) {
@@ -166,14 +167,14 @@ int race_autotune(race_schedule* s, int32_t k, const double* X_d, double* B_d, i
             }
             if (df)
                 for (int g : {1, 2})
-                    for (int q : {1, 2})
+                    for (int q : {0, 1, 2})
                         for (int u : {4, 8}) cand.push_back({RACE_EXEC_DF64_RED, g, 1, bps, u, q});
         } else {
             if (bps != 6)
                 for (int r : {1, 2, 4}) cand.push_back({RACE_EXEC_ROWS_RED, 1, r, bps, 8, 0});
             if (df)
                 for (int r : {1, 2})
-                    for (int q : {1, 2}) cand.push_back({RACE_EXEC_DF64_RED, 1, r, bps, 4, q});
+                    for (int q : {0, 1, 2}) cand.push_back({RACE_EXEC_DF64_RED, 1, r, bps, 4, q});
         }
     }
     const race_launch keep = s->launch;

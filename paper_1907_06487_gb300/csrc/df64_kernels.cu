@@ -1,5 +1,5 @@
-// SymmSpMV with the transposed products on the FP32 and integer pipes
-// (executor RACE_EXEC_DF64_RED).
+// SymmSpMV with the transposed products off the FP64 pipe (executor
+// RACE_EXEC_DF64_RED).
 //
 // GB300 runs FP64 at about 1/70 of its FP32 rate.  The FP64 SymmSpMV (Alg.
 // "SymmSpMV") issues one FP64 multiply-add per stored upper entry for the row
@@ -7,20 +7,22 @@
 // on the 4-body XXZ Hamiltonian (26 sites) 151 M FP64 operations, 0.30 ms at
 // the measured 0.5 T/s, against 0.17 ms of HBM traffic.  Here the row sums
 // stay exact FP64 multiply-adds (80.7 M, 0.16 ms of FP64 pipe) and each
-// transposed update a_ij x_i is formed in double-float arithmetic
-// (df64.cuh): a_ij split with integer operations, x_i split once per row,
-// Dekker's product on the FP32 pipe, and the pair reassembled into a double
-// with integer operations before its reduction at L2.  b, x and the stored
-// values stay FP64.
+// transposed update a_ij x_i of a share of the row groups is formed on the
+// integer pipes (int_product.cuh): x_i prepared once per row, the two
+// significands multiplied in 32-bit pieces, sign and exponent added as bit
+// fields, the result a double ready for its reduction at L2.  The other row
+// groups multiply in FP64, so the two pipes share the work.  b, x and the
+// stored values stay FP64.  (Dekker's double-float product on the FP32 pipe,
+// df64.cuh, did this job before: about 30 integer and FP32 instructions per
+// update against about 15, and an error of 2^-44 against 2^-51.)
 //
-// Accuracy: every transposed update carries a relative error below 2^-44
-// (split, product and reassembly; checked exhaustively against rational
-// arithmetic by the CPU tests), so |b_i - exact| stays below
-// (2^-44 + n_i 2^-53) sum_j |a_ij x_j| for any row length: inside
-// 1e-12 sum_j |a_ij x_j|.  Rows whose x_i is zero contribute no updates;
-// rows whose x_i lies outside the split's range [2^-50, 2^51) scatter in
-// FP64.  Stored off-diagonal values must be zero or inside that range
-// (checked once when the executor is prepared).
+// Accuracy: every transposed update is the exact product truncated, within
+// 2^-51 of it (checked against rational arithmetic by the CPU tests), so
+// |b_i - exact| stays below (2^-51 + n_i 2^-53) sum_j |a_ij x_j| for any row
+// length: inside 1e-12 sum_j |a_ij x_j|.  Rows whose x_i is zero contribute
+// no updates; rows whose x_i lies outside [2^-50, 2^51) scatter in FP64.
+// Stored off-diagonal values must be zero or inside that range (checked once
+// when the executor is prepared).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +31,7 @@
 
 #include "df64.cuh"
 #include "fp64_share.cuh"
+#include "int_product.cuh"
 #include "race_internal.h"
 
 namespace {
@@ -56,15 +59,15 @@ __host__ __device__ __forceinline__ bool out_of_range(float v) {
 }
 
 // How a row scatters its transposed part.
-enum Scatter { kSplit = 0, kFp64 = 1, kNone = 2 };
+enum Scatter { kIntProd = 0, kFp64 = 1, kNone = 2 };
 
 // One row's share of one lane: FP64 row sum returned, transposed updates
 // sent to b.  B (4 or 8) independent entries per lane and iteration.
 template <typename VT, int G, int MODE, int B>
 __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, int lane,
                                            const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                           const double* __restrict__ x, double* b, double xr, float xrh,
-                                           float xrl) {
+                                           const double* __restrict__ x, double* b, double xr,
+                                           const intprod::Factor& xf) {
     double acc = 0.0;
     for (int32_t idx = lo + lane; idx < hi; idx += B * G) {
         VT a[B];
@@ -83,13 +86,8 @@ __device__ __forceinline__ double lane_row(int32_t row, int32_t lo, int32_t hi, 
         for (int t = 0; t < B; ++t) {
             if (c[t] < 0) continue;
             acc = fma(df64::widen(a[t]), xc[t], acc);
-            if constexpr (MODE == kSplit) {
-                if (c[t] != row && !df64::is_zero(a[t])) {
-                    float ah, al, ph, pl;
-                    df64::split_value(a[t], ah, al);
-                    df64::mul(ah, al, xrh, xrl, ph, pl);
-                    atomicAdd(b + c[t], df64::join(ph, pl));
-                }
+            if constexpr (MODE == kIntProd) {
+                if (c[t] != row && !df64::is_zero(a[t])) atomicAdd(b + c[t], intprod::mul(a[t], xf));
             } else if constexpr (MODE == kFp64) {
                 if (c[t] != row) atomicAdd(b + c[t], df64::widen(a[t]) * xr);
             }
@@ -109,12 +107,13 @@ __device__ __forceinline__ void row_df64(int32_t row, int lane, unsigned mask, b
     const int32_t lo = __ldg(rp + row), hi = __ldg(rp + row + 1);
     const double xr = __ldg(x + row);
     float xrh, xrl;
-    const int st = df64::split(xr, xrh, xrl);
+    const int st = df64::split(xr, xrh, xrl);  // the range test of x_i
+    const intprod::Factor xf = intprod::factor(xr);
     double acc;
-    if (st != 0) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-    else if (xrh == 0.0f) acc = lane_row<VT, G, kNone, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-    else if (warp64) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
-    else acc = lane_row<VT, G, kSplit, B>(row, lo, hi, lane, col, val, x, b, xr, xrh, xrl);
+    if (st != 0) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xf);
+    else if (xrh == 0.0f) acc = lane_row<VT, G, kNone, B>(row, lo, hi, lane, col, val, x, b, xr, xf);
+    else if (warp64) acc = lane_row<VT, G, kFp64, B>(row, lo, hi, lane, col, val, x, b, xr, xf);
+    else acc = lane_row<VT, G, kIntProd, B>(row, lo, hi, lane, col, val, x, b, xr, xf);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
     if (lane == 0) atomicAdd(b + row, acc);
@@ -128,8 +127,9 @@ __global__ void __launch_bounds__(kBlock) k_symm_df64(int32_t n, const int32_t* 
     const int lane = threadIdx.x & (G - 1);
     const unsigned mask = lane_mask<G>();
     // fp64_quarters of every four warp-wide row groups scatter with FP64
-    // multiplies (warp-uniform, spread over the SM's FP64 units), the rest in
-    // double-float: the work is shared between the FP64 and integer pipes
+    // multiplies (warp-uniform, spread over the SM's FP64 units), the rest by
+    // the integer product: the work is shared between the FP64 and integer
+    // pipes
     const int64_t gid = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) / G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * kBlock / G;
     for (int64_t r = gid; r < n; r += ngroups) {
@@ -214,7 +214,7 @@ int race_df64_prepare(const race_schedule* s) {
         s->df64_state.store(st, std::memory_order_release);
     }
     if (st == -1) {
-        race_set_detail("an off-diagonal value outside the double-float magnitude range [2^-50, 2^51)");
+        race_set_detail("an off-diagonal value outside the magnitude range [2^-50, 2^51) of the integer product");
         return RACE_ERR_UNSUPPORTED;
     }
     return RACE_OK;

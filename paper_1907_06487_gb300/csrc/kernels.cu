@@ -16,6 +16,7 @@
 #include <cstdint>
 
 #include "df64.cuh"
+#include "int_product.cuh"
 #include "fp64_share.cuh"
 #include "race_internal.h"
 
@@ -417,10 +418,10 @@ __global__ void __launch_bounds__(kBlock) k_rows_pipe(int32_t n, const int32_t* 
 // group of K lanes owns a row, lane c serves column c, so the K values of
 // a row of X or B are contiguous across the group.  Updates of B are
 // reductions at L2 (B zeroed before).  R rows per group in flight.
-// DF: the transposed updates a_ij X[i][c] in double-float arithmetic on the
-// FP32 and integer pipes (df64.cuh; off-diagonal values range-checked once),
-// the row sums stay FP64; a row whose X[i][c] lies outside the split's range
-// scatters that column in FP64 after its main loop.
+// DF: the transposed updates a_ij X[i][c] by the integer product of the
+// significands (int_product.cuh; off-diagonal values range-checked once),
+// the row sums stay FP64; a row whose X[i][c] lies outside the range
+// [2^-50, 2^51) scatters that column in FP64 after its main loop.
 template <typename VT, int K, int R, bool DF>
 __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const int32_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
         int32_t js[R], je[R];
         double xr[R], acc[R];
         float xrh[R], xrl[R];
+        intprod::Factor xf[R];
         bool xr64[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -445,7 +447,8 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
             je[q] = v ? __ldg(rp + r + 1) : 0;
             xr[q] = v ? __ldg(X + r * K + c) : 0.0;
             acc[q] = 0.0;
-            xr64[q] = DF && df64::split(xr[q], xrh[q], xrl[q]) != 0;
+            xr64[q] = DF && df64::split(xr[q], xrh[q], xrl[q]) != 0;  // the range test of x_r
+            xf[q] = intprod::factor(xr[q]);
         }
         int32_t len = 0;
 #pragma unroll
@@ -483,10 +486,7 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
                         if (warp64) {  // warp-uniform: this warp's share of FP64 products
                             if (!xr64[q]) atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, a * xr[q]);
                         } else if (xrh[q] != 0.0f && !df64::is_zero(araw[q][u])) {
-                            float ah, al, ph, pl;
-                            df64::split_value(araw[q][u], ah, al);
-                            df64::mul(ah, al, xrh[q], xrl[q], ph, pl);
-                            atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, df64::join(ph, pl));
+                            atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, intprod::mul(araw[q][u], xf[q]));
                         }
                     } else {
                         atomicAdd(B + static_cast<int64_t>(cc[q][u]) * K + c, a * xr[q]);
@@ -509,9 +509,9 @@ __global__ void __launch_bounds__(kBlock) k_symm_mm_rows_red(int32_t n, const in
     }
 }
 
-// How a row of the double-float SymmSpMM forms its transposed products:
-// split (double-float), FP64 multiplies, or none (x_r is zero).
-enum MmScatter { kMmSplit = 0, kMmFp64 = 1, kMmNone = 2 };
+// How a row of k_symm_mm_rows_df forms its transposed products: the integer
+// product (int_product.cuh), FP64 multiplies, or none (x_r is zero).
+enum MmScatter { kMmIntProd = 0, kMmFp64 = 1, kMmNone = 2 };
 
 // One row of k_symm_mm_rows_df for the lane of right-hand side c: the FP64
 // row sum is returned, the transposed updates go to B as reductions.  The
@@ -520,7 +520,7 @@ enum MmScatter { kMmSplit = 0, kMmFp64 = 1, kMmNone = 2 };
 template <typename VT, int K, int MODE>
 __device__ __forceinline__ double mm_row_df(int32_t js, int32_t je, int c, const int32_t* __restrict__ col,
                                             const VT* __restrict__ val, const double* __restrict__ X, double* B,
-                                            double xr, float xrh, float xrl) {
+                                            double xr, const intprod::Factor& xf) {
     double acc = 0.0;
     constexpr int U = 4;
     for (int32_t p = js; p < je; p += U) {
@@ -541,13 +541,8 @@ __device__ __forceinline__ double mm_row_df(int32_t js, int32_t je, int c, const
             const double a = df64::widen(araw[u]);
             acc = fma(a, xc[u], acc);
             if (p + u == js) continue;  // the diagonal (first entry) has no transposed update
-            if constexpr (MODE == kMmSplit) {
-                if (!df64::is_zero(araw[u])) {
-                    float ah, al, ph, pl;
-                    df64::split_value(araw[u], ah, al);
-                    df64::mul(ah, al, xrh, xrl, ph, pl);
-                    atomicAdd(B + static_cast<int64_t>(cc[u]) * K + c, df64::join(ph, pl));
-                }
+            if constexpr (MODE == kMmIntProd) {
+                if (!df64::is_zero(araw[u])) atomicAdd(B + static_cast<int64_t>(cc[u]) * K + c, intprod::mul(araw[u], xf));
             } else if constexpr (MODE == kMmFp64) {
                 atomicAdd(B + static_cast<int64_t>(cc[u]) * K + c, a * xr);
             }
@@ -556,12 +551,12 @@ __device__ __forceinline__ double mm_row_df(int32_t js, int32_t je, int c, const
     return acc;
 }
 
-// SymmSpMM with double-float transposed products, one row per group of K
-// lanes (lane c owns right-hand side c) and rows strided over the grid.  The
-// lane's mode for the row: x_r outside the split's range or a row group of
-// the FP64 share (warp-uniform, fp64_quarters of every four, spread over the
-// SM's FP64 units): FP64 multiplies; x_r zero: no transposed updates; else
-// double-float.
+// SymmSpMM with the transposed products off the FP64 pipe, one row per group
+// of K lanes (lane c owns right-hand side c) and rows strided over the grid.
+// The lane's mode for the row: x_r outside the range [2^-50, 2^51) or a row
+// group of the FP64 share (warp-uniform, fp64_quarters of every four, spread
+// over the SM's FP64 units): FP64 multiplies; x_r zero: no transposed
+// updates; else the integer product of the significands.
 template <typename VT, int K>
 __global__ void __launch_bounds__(kBlock, 6) k_symm_mm_rows_df(int32_t n, const int32_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
@@ -575,11 +570,12 @@ __global__ void __launch_bounds__(kBlock, 6) k_symm_mm_rows_df(int32_t n, const 
         const int32_t js = __ldg(rp + r), je = __ldg(rp + r + 1);
         const double xr = __ldg(X + r * K + c);
         float xrh, xrl;
-        const int st = df64::split(xr, xrh, xrl);
+        const int st = df64::split(xr, xrh, xrl);  // the range test of x_r
+        const intprod::Factor xf = intprod::factor(xr);
         double acc;
-        if (st != 0 || warp64) acc = mm_row_df<VT, K, kMmFp64>(js, je, c, col, val, X, B, xr, xrh, xrl);
-        else if (xrh == 0.0f) acc = mm_row_df<VT, K, kMmNone>(js, je, c, col, val, X, B, xr, xrh, xrl);
-        else acc = mm_row_df<VT, K, kMmSplit>(js, je, c, col, val, X, B, xr, xrh, xrl);
+        if (st != 0 || warp64) acc = mm_row_df<VT, K, kMmFp64>(js, je, c, col, val, X, B, xr, xf);
+        else if (xrh == 0.0f) acc = mm_row_df<VT, K, kMmNone>(js, je, c, col, val, X, B, xr, xf);
+        else acc = mm_row_df<VT, K, kMmIntProd>(js, je, c, col, val, X, B, xr, xf);
         atomicAdd(B + r * K + c, acc);
     }
 }

@@ -31,8 +31,9 @@
 //                       blocks) fits there.
 //
 // Arithmetic as RACE_EXEC_DF64_RED: FP64 row sums; the transposed products
-// in FP64 in fp64_quarters / 4 of each warp's row groups and in double-float
-// in the rest (relative error below 2^-44 each).  The columns of Y are read through L2
+// in FP64 in fp64_quarters / 4 of each warp's row groups and by the integer
+// product of the significands (int_product.cuh) in the rest (relative error
+// below 2^-51 each).  The columns of Y are read through L2
 // only (ld.global.cg): they are written by reductions during the launch.
 // Every wait on a done flag is bounded; one that gives up records
 // RACE_ERR_TIMEOUT in the schedule's status word and its block leaves the
@@ -45,6 +46,7 @@
 #include <vector>
 
 #include "df64.cuh"
+#include "int_product.cuh"
 #include "fp64_share.cuh"
 #include "race_internal.h"
 #include "red.cuh"
@@ -79,7 +81,8 @@ __device__ __forceinline__ void warp_rows(int32_t row, bool live, const int32_t*
     const int32_t maxlen = __reduce_max_sync(kFull, len);
     const double xr = live ? __ldcg(src + row) : 0.0;
     float xrh = 0.0f, xrl = 0.0f;
-    const int xbad = df64::split(xr, xrh, xrl);
+    const int xbad = df64::split(xr, xrh, xrl);  // the range test of x_i
+    const intprod::Factor xf = intprod::factor(xr);
     const bool use64 = tp64 || __any_sync(kFull, live && xbad != 0);  // warp-uniform choice
     const bool scatter = !df64::is_zero(xr);
     double acc = 0.0;
@@ -102,10 +105,7 @@ __device__ __forceinline__ void warp_rows(int32_t row, bool live, const int32_t*
             if (use64) {
                 red_add_f64(dst + c[u], a[u] * xr);
             } else if (!df64::is_zero(a[u])) {
-                float ah, al, ph, pl;
-                df64::split_in_range(a[u], ah, al);
-                df64::mul(ah, al, xrh, xrl, ph, pl);
-                red_add_f64(dst + c[u], df64::join(ph, pl));
+                red_add_f64(dst + c[u], intprod::mul(a[u], xf));
             }
         }
     }

@@ -164,7 +164,8 @@ struct race_schedule {
     uint32_t* d_bar = nullptr;    // one-launch executors: barrier words, leaf tickets, block ranking
     int32_t max_row_upper = 0, max_row_full = 0;
     WindowSet win_red, win_race;  // window executors (flat tiles / RACE leaves)
-    // double-float executor: off-diagonal values range-checked on first use
+    // executor with the transposed products off the FP64 pipe: off-diagonal
+    // values range-checked on first use
     // (0 = not checked, 1 = ready, -1 = a value out of range)
     mutable std::atomic<int32_t> df64_state{0};
     mutable SellSet sell;  // built on first use of RACE_EXEC_SELL_DF64
@@ -196,7 +197,7 @@ int race_window_launch(const race_schedule* s, bool race_mode, const double* x, 
 // device work) and the launch, which prepares on first use.
 int race_df64_prepare(const race_schedule* s);
 int race_df64_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
-// The double-float arithmetic phase by phase (RACE_EXEC_PHASE_DF64).
+// The arithmetic of RACE_EXEC_DF64_RED phase by phase (RACE_EXEC_PHASE_DF64).
 int race_df64_phase_launch(const race_schedule* s, const double* x, double* b, cudaStream_t st);
 // Rows of a phase one block of RACE_EXEC_PHASE_DF64 takes at a time.
 constexpr int32_t kPhaseBlockRows = 256;

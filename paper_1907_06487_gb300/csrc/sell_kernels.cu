@@ -16,8 +16,9 @@
 // value 0.
 //
 // Arithmetic as RACE_EXEC_DF64_RED: FP64 row sums (one multiply-add per
-// entry), transposed updates a_ij x_i in double-float arithmetic
-// (df64.cuh), both sent to b as reductions at L2 on a zeroed b.
+// entry), transposed updates a_ij x_i by the integer product of the
+// significands (int_product.cuh), both sent to b as reductions at L2 on a
+// zeroed b.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +28,7 @@
 #include <vector>
 
 #include "df64.cuh"
+#include "int_product.cuh"
 #include "race_internal.h"
 
 namespace {
@@ -57,8 +59,9 @@ __global__ void __launch_bounds__(kBlock) k_symm_sell(int64_t n_chunks, const in
         const int32_t row = __ldg(srow + k * kChunk + lane);
         const double xr = row >= 0 ? __ldg(x + row) : 0.0;
         float xrh, xrl;
-        const int st = df64::split(xr, xrh, xrl);
+        const int st = df64::split(xr, xrh, xrl);  // the range test of x_r
         const bool scatter = st == 0 && xrh != 0.0f;
+        const intprod::Factor xf = intprod::factor(xr);
         const VT* vp = val + o + lane;
         const int32_t* cp = col + o + lane;
         double acc = 0.0;
@@ -77,12 +80,8 @@ __global__ void __launch_bounds__(kBlock) k_symm_sell(int64_t n_chunks, const in
 #pragma unroll
             for (int t = 0; t < U; ++t) {
                 acc = fma(df64::widen(a[t]), xc[t], acc);
-                if (scatter && c[t] >= 0 && c[t] != row && !df64::is_zero(a[t])) {
-                    float ah, al, ph, pl;
-                    df64::split_value(a[t], ah, al);
-                    df64::mul(ah, al, xrh, xrl, ph, pl);
-                    atomicAdd(b + c[t], df64::join(ph, pl));
-                }
+                if (scatter && c[t] >= 0 && c[t] != row && !df64::is_zero(a[t]))
+                    atomicAdd(b + c[t], intprod::mul(a[t], xf));
             }
         }
         if (st != 0) {  // x_row outside the split's range: this row scatters in FP64

@@ -23,8 +23,8 @@
 // (by quarters of the warp index) the row sums run either as FP64 fused
 // multiply-adds or in double-float arithmetic (df64.cuh: Dekker products of
 // the split operands, summed as a float pair with Knuth's TwoSum), and the
-// transposed products either as FP64 multiplies or as Dekker products joined
-// into a double.  The FP64 row sums go to the first quarters and the FP64
+// transposed products either as FP64 multiplies or by the integer product of
+// the significands (int_product.cuh).  The FP64 row sums go to the first quarters and the FP64
 // transposed products to the last ones, so a warp does at most one FP64
 // operation per stored entry unless both shares exceed half.  x, b and the
 // stored values stay FP64 (or FP32-stored values, widened exactly).
@@ -49,6 +49,7 @@
 #include <string>
 
 #include "df64.cuh"
+#include "int_product.cuh"
 #include "race_internal.h"
 #include "stream_engine.cuh"
 #include "red.cuh"
@@ -137,7 +138,8 @@ __device__ __forceinline__ void tile_rows(int32_t row, bool live, int32_t lo, in
                                           const double* __restrict__ x, double* b) {
     const double xr = live ? __ldg(x + row) : 0.0;
     float xrh = 0.0f, xrl = 0.0f;
-    const int xr_bad = TP64 ? 0 : df64::split(xr, xrh, xrl);
+    const int xr_bad = TP64 ? 0 : df64::split(xr, xrh, xrl);  // the range test of x_i
+    const intprod::Factor xf = intprod::factor(xr);
     const bool scatter = !df64::is_zero(xr);  // x_i = 0: the row makes no transposed update
     const bool rs_df = !RS64 && len <= kDfRowMax;
     double acc = 0.0;
@@ -183,9 +185,7 @@ __device__ __forceinline__ void tile_rows(int32_t row, bool live, int32_t lo, in
                     if (abad | xr_bad) {
                         defer = true;
                     } else if (!df64::is_zero(a[u])) {
-                        float ph, pl;
-                        df64::mul(ah, al, xrh, xrl, ph, pl);
-                        red_add_f64(b + c[u], df64::join(ph, pl));
+                        red_add_f64(b + c[u], intprod::mul(a[u], xf));
                     }
                 }
             }

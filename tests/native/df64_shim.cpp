@@ -1,7 +1,6 @@
-// Host build of the double-float helpers used by the SymmSpMV executor that
-// forms the transposed products on the FP32 and integer pipes, exported for
-// the CPU tests (compiled with contraction off, so every FP32 operation
-// rounds exactly as on the device).
+// Host build of the double-float helpers (the staged executor's row sums, the
+// range test of x_i), exported for the CPU tests (compiled with contraction
+// off, so every FP32 operation rounds exactly as on the device).
 #include <initializer_list>
 
 #include "../../paper_1907_06487_gb300/csrc/df64.cuh"
@@ -20,8 +19,8 @@ void df_two_sum(float a, float b, float* s, float* e) { df64::two_sum(a, b, *s, 
 
 void df_fast_two_sum(float a, float b, float* s, float* e) { df64::fast_two_sum(a, b, *s, *e); }
 
-// One transposed contribution a * xr as the kernel forms it: a (nonzero,
-// in range) split without a test, xr split with the test; an xr outside the
+// A product a * xr of split doubles joined into a double: a (nonzero, in
+// range) split without a test, xr split with the test; an xr outside the
 // range is multiplied in FP64, a zero xr gives no contribution.
 double df_scatter(double a, double xr) {
     float xh, xl;

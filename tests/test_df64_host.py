@@ -1,12 +1,11 @@
-"""CPU checks of the double-float helpers behind the SymmSpMV executor that
-forms the transposed products on the FP32 and integer pipes
-(paper_1907_06487_gb300/csrc/df64.cuh), compiled for the host with
-contraction off and checked against exact rational arithmetic: the split of a
-double into two floats (with and without the range test), the error-free
-sums, the product, the branch-free integer reassembly into a double, and the
-whole transposed contribution a * x_r.  The bounds are the ones the header
-states; the last one (2^-44 of |a x_r|) is what the executor's accuracy
-claim rests on."""
+"""CPU checks of the double-float helpers (paper_1907_06487_gb300/csrc/df64.cuh)
+behind the staged SymmSpMV executor's double-float row sums and the range
+test of x_i in every executor that forms products off the FP64 pipe,
+compiled for the host with contraction off and checked against exact
+rational arithmetic: the split of a double into two floats (with and without
+the range test), the error-free sums, the product, the branch-free integer
+reassembly into a double, and a product of split doubles joined back into a
+double.  The bounds are the ones the header states."""
 import ctypes
 import math
 import os

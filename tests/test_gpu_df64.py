@@ -1,9 +1,10 @@
-"""GPU parity of the SymmSpMV executors with double-float transposed updates
-(RACE_EXEC_DF64_RED on the CRS, RACE_EXEC_SELL_DF64 on a SELL-32-sigma copy)
+"""GPU parity of the SymmSpMV executors that form the transposed updates off
+the FP64 pipe, by an integer product of the significands (RACE_EXEC_DF64_RED
+on the CRS, RACE_EXEC_SELL_DF64 on a SELL-32-sigma copy)
 against the CPU oracle, under the FP64 bound
 |b_i - b_ref_i| <= 1e-12 sum_j |a_ij||x_j|: every lane count, FP32 values,
 entries per step of the SELL kernel, x entries that are zero or outside the
-split's range (those rows scatter in FP64), long rows on one lane, explicit zeros and large diagonal values, a
+range [2^-50, 2^51) (those rows scatter in FP64), long rows on one lane, explicit zeros and large diagonal values, a
 diagonal matrix and a single row, and the refusal of off-diagonal values
 outside the range."""
 import numpy as np
@@ -227,10 +228,10 @@ def test_natural_order(dev, oracle_mod, matgen_mod, exe):
     check(run(s, x, dev, exe), bref, sc)
 
 
-@pytest.mark.parametrize("quarters", [1, 2, 4])
+@pytest.mark.parametrize("quarters", [0, 1, 2, 4])
 def test_fp64_share_of_transposed_updates(dev, oracle_mod, matgen_mod, quarters):
     """fp64_quarters: that share of the warps forms its transposed updates with
-    FP64 multiplies, the rest in double-float; same bound either way (SpMV
+    FP64 multiplies, the rest by the integer product; same bound either way (SpMV
     and SpMM, x with zeros and out-of-range entries)."""
     m = matgen_mod.stencil3d(15, npt=27, seed=9)
     s = R.race_build(m, 16)

@@ -189,7 +189,7 @@ def test_full_size_xxz26(dev, oracle_mod):
         assert_parity(b[rows], bref, sc)
     # property at every row: the uniform vector is an eigenvector, eigenvalue L/4 = 6.5,
     # and every partial sum is a multiple of 1/4 (exact in FP64, and in the
-    # double-float products: 0.5 * 1 splits exactly)
+    # integer products: 0.5 * 1 has a short significand, so truncation is exact)
     ones = np.ones(n)
     assert np.all(run_symm(s, m, ones, dev) == 6.5)
     b1 = run_symm(s, m, ones, dev, cfg["executor"])

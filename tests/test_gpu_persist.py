@@ -1,6 +1,7 @@
 """GPU parity of the one-launch RACE executors (RACE_EXEC_PERSIST_GROUP: one
 leaf per lane group, plain updates of b; RACE_EXEC_PERSIST_CTA: one leaf per
-block) and of the phase-by-phase double-float executor
+block) and of the phase-by-phase executor with the transposed products off
+the FP64 pipe
 (RACE_EXEC_PHASE_DF64: one launch per phase over the leaves' rows in chunks)
 against the CPU oracle, under the FP64 bound
 |b_i - b_ref_i| <= 1e-12 sum_j |a_ij||x_j|.
@@ -171,7 +172,7 @@ PD = R.RACE_EXEC_PHASE_DF64
 @pytest.mark.parametrize("per_step,quarters", [(4, 2), (8, 1), (4, 0), (4, 4)])
 @pytest.mark.parametrize("which", sorted(MATS))
 def test_phase_df64(dev, oracle_mod, matgen_mod, which, per_step, quarters):
-    # the double-float arithmetic phase by phase, the leaves' rows in chunks
+    # RACE_EXEC_DF64_RED's arithmetic phase by phase, the leaves' rows in chunks
     # of at most 256 rows: deep schedules (many phases, leaves of a few rows)
     # and depth-1 ones (few phases, leaves of thousands of rows)
     m = MATS[which](matgen_mod)

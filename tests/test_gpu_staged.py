@@ -1,9 +1,11 @@
 """GPU parity of the warp-tile staged SymmSpMV (RACE_EXEC_STAGED: values and
-columns brought into shared memory by bulk copies, row sums and transposed
-products in FP64 or double-float per quarter of the warps) against the CPU
+columns brought into shared memory by bulk copies, row sums in FP64 or
+double-float and transposed products in FP64 or by the integer product of the
+significands, per quarter of the warps) against the CPU
 oracle, under the FP64 bound |b_i - b_ref_i| <= 1e-12 sum_j |a_ij||x_j|.
 
-Cases: every mix of FP64 and double-float row sums and transposed products,
+Cases: every mix of FP64 and double-float row sums with FP64 and integer
+transposed products,
 4 and 8 entries per lane and step, ragged last tiles, variable row lengths,
 FP32-stored values, x entries that are zero or outside the split's range,
 stored values outside it (taken in FP64, not refused), tiles too long to
