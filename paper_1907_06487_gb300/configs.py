@@ -25,8 +25,8 @@ SEEDS = {"anderson32": (1, 2), "xxz26": (None, 3), "st27_200": (4, 5)}
 # schedule parameters per workload: n_workers, eps, max_depth, the executor
 # tested at full size, and the launch shapes of symm_spmv / spmv_full
 # (shapes from the measured sweeps on GB300: one row per thread wins; FP64
-# row sums with double-float transposed updates are at least as fast as
-# all-FP64 on every workload).  The recursion stops after stage 1 (two
+# row sums with most transposed products formed on the integer pipes are
+# faster than all-FP64 on every workload).  The recursion stops after stage 1 (two
 # colours of level groups, Sec. 4.4.3): the executors that take the
 # transposed update through L2 reductions use the schedule's permutation,
 # not its phases, and the stage-0 level order keeps neighbours close while

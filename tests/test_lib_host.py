@@ -147,8 +147,8 @@ def test_host_only_schedule_refuses_compute(lib):
     with pytest.raises(R.RaceError) as e:
         R.symm_spmv(s, 0x1000, 0x2000)
     assert e.value.code == R.RACE_ERR_UNSUPPORTED
-    # launch shapes are checked before anything else; the double-float
-    # executor needs a device schedule
+    # launch shapes are checked before anything else; the executor with the
+    # transposed products off the FP64 pipe needs a device schedule
     for bad in (dict(fp64_quarters=5), dict(fp64_quarters=-1), dict(group_lanes=3), dict(executor=99)):
         with pytest.raises(R.RaceError) as e:
             R.race_set_launch(s, 0, **dict(dict(executor=R.RACE_EXEC_DF64_RED, group_lanes=1, rows_per_group=1), **bad))
