@@ -115,3 +115,19 @@ def test_scatter_contributions(ip):
     assert ip.ip_scatter(3.0, 2.0 ** 70) == 3.0 * 2.0 ** 70  # x outside the range: FP64
     assert ip.ip_scatter(3.0, 2.0 ** -60) == 3.0 * 2.0 ** -60
     assert math.isnan(ip.ip_scatter(3.0, math.nan))
+
+
+def test_dropped_partial_products_at_their_largest(ip):
+    """Significands whose low words are all ones make the dropped low by low
+    product and the dropped carries of the cross products as large as they
+    get: the result still sits at most one unit below the truncation."""
+    rng = np.random.default_rng(14)
+    low_ones = (1 << 21) - 1  # a significand's low 32 bits sit in bits 0..20 of the stored field, left-aligned by 11
+    for _ in range(5000):
+        bits = []
+        for _ in range(2):
+            hi = int(rng.integers(0, 1 << 31)) << 21
+            e = int(rng.integers(-50, 51))
+            bits.append((int(rng.integers(0, 2)) << 63) | ((e + 1023) << 52) | ((hi | low_ones) & ((1 << 52) - 1)))
+        a, x = (struct.unpack("<d", struct.pack("<Q", b))[0] for b in bits)
+        check(ip.ip_mul(a, x), Fraction(a) * Fraction(x))
