@@ -21,7 +21,9 @@ written: the count of Eq. "SymmSpMV_intensity" at the optimal alpha, which
 the reduction-based executors also move: b is zeroed, accumulated in L2 and
 written back) over the launch's CUDA-event time, against the measured copy
 bandwidth and, as the paper's range, the load-only bandwidth measured here;
-SymmSpMM also against min(HBM * I, FP64 FMA rate measured here).
+SymmSpMM also against min(HBM * I, FP64 roof), the FP64 roof being the
+FP64 FMA rate measured here over the row sums' multiply-adds, the FP64 work
+that stays on the FP64 pipe (the all-FP64 roof is given beside it).
 
 Timing: W warm-up steps, then K steps bracketed by a barrier and
 torch.cuda.synchronize(), CUDA events on the stream the kernels run on;
